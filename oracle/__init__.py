@@ -1,0 +1,187 @@
+"""Reference oracle for the six generators -- TEST INFRASTRUCTURE ONLY.
+
+This package wraps ``prng_oracle.c``, a plain single-threaded C implementation
+written from the paper's definitions (Demchik, arXiv:1003.1898, Section 3 and
+Appendix A).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it.  The library (``paper_1003_1898_gb300``)
+never imports it and shares no code with it.
+
+Parity unpinned (partially): the RANECU combination step and the XOR128
+known answer; see the header of ``prng_oracle.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "prng_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GGL, XOR128, RANECU, RANMAR, RANLUX, MT19937 = range(6)
+NAMES = ("ggl", "xor128", "ranecu", "ranmar", "ranlux", "mt19937")
+GEN_IDS = {n: i for i, n in enumerate(NAMES)}
+SHIFT = {GGL: 7, RANECU: 7, XOR128: 8, MT19937: 8, RANMAR: 0, RANLUX: 0}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, no vector intrinsics)."""
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "prng_oracle.h")))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-I", _HERE])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _u64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _u32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def _f32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+            vp = ctypes.c_void_p
+            L.orc_splitmix64.restype = u64
+            L.orc_splitmix64.argtypes = [u64]
+            L.orc_fill.restype = ctypes.c_int
+            L.orc_fill.argtypes = [i32, i32, u64, u64, u32, u64, u64, vp, vp]
+            L.orc_sample.restype = ctypes.c_int
+            L.orc_sample.argtypes = [i32, i32, u64, u64, vp, u64, vp]
+            L.orc_modpow.restype = u64
+            L.orc_modpow.argtypes = [u64, u64, u64]
+            L.orc_ggl_jump.restype = u32
+            L.orc_ggl_jump.argtypes = [u32, u64]
+            L.orc_serial_sample.restype = ctypes.c_int
+            L.orc_serial_sample.argtypes = [i32, u64, vp, u64, vp]
+            L.orc_serial_fill.restype = ctypes.c_int
+            L.orc_serial_fill.argtypes = [i32, u64, u64, vp]
+            L.orc_explicit_draws.restype = ctypes.c_int
+            L.orc_explicit_draws.argtypes = [i32, i32, vp, u32, u64, vp]
+            L.orc_checksum_draws.restype = u64
+            L.orc_checksum_draws.argtypes = [i32, i32, u64, u64, u64]
+            L.orc_luxury_p.restype = i32
+            L.orc_luxury_p.argtypes = [i32]
+            L.orc_to_f32.restype = ctypes.c_float
+            L.orc_to_f32.argtypes = [i32, u32]
+            L.orc_ranecu_comp1.restype = u32
+            L.orc_ranecu_comp1.argtypes = [ctypes.POINTER(i32)]
+            L.orc_ranecu_comp2.restype = u32
+            L.orc_ranecu_comp2.argtypes = [ctypes.POINTER(i32)]
+            _lib = L
+    return _lib
+
+
+def gen_id(gen) -> int:
+    return GEN_IDS[gen] if isinstance(gen, str) else int(gen)
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(x & (2**64 - 1)))
+
+
+def luxury_p(luxury: int) -> int:
+    return int(lib().orc_luxury_p(luxury))
+
+
+def fill(gen, seed: int, n_streams: int, n_per: int, *, luxury: int = 0,
+         stream0: int = 0, skip: int = 0, want_f32: bool = False):
+    """Stream-major draws of streams [stream0, stream0+n_streams), each after
+    discarding `skip` draws.  Returns u32 (and f32) arrays of shape
+    (n_streams, n_per)."""
+    g = gen_id(gen)
+    u = np.zeros((n_streams, n_per), dtype=np.uint32)
+    f = np.zeros((n_streams, n_per), dtype=np.float32) if want_f32 else None
+    rc = lib().orc_fill(g, luxury, seed & (2**64 - 1), stream0, n_streams, skip, n_per,
+                        u.ctypes.data, f.ctypes.data if f is not None else None)
+    if rc != 0:
+        raise ValueError("oracle fill rejected its arguments")
+    return (u, f) if want_f32 else u
+
+
+def sample(gen, seed: int, stream: int, positions, *, luxury: int = 0):
+    """Draws at sorted 0-based positions of one stream."""
+    pos = np.ascontiguousarray(np.asarray(positions, dtype=np.uint64))
+    out = np.zeros(pos.shape[0], dtype=np.uint32)
+    rc = lib().orc_sample(gen_id(gen), luxury, seed & (2**64 - 1), stream,
+                          pos.ctypes.data, pos.shape[0], out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle sample rejected its arguments")
+    return out
+
+
+def to_f32(gen, v):
+    """Exact float conversion, computed in float64 then narrowed."""
+    g = gen_id(gen)
+    v = np.asarray(v, dtype=np.uint64)
+    return ((v >> np.uint64(SHIFT[g])).astype(np.float64) / 16777216.0).astype(np.float32)
+
+
+def explicit_draws(gen, seeds, n: int, *, luxury: int = 0):
+    """n draws of a stream initialised from explicit seeds (see the C header)."""
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    out = np.zeros(n, dtype=np.uint32)
+    rc = lib().orc_explicit_draws(gen_id(gen), luxury, sd.ctypes.data, sd.shape[0], n,
+                                  out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle explicit_draws rejected its arguments")
+    return out
+
+
+def modpow(a: int, e: int, m: int) -> int:
+    return int(lib().orc_modpow(a, e, m))
+
+
+def ggl_jump(x: int, k: int) -> int:
+    return int(lib().orc_ggl_jump(x, k))
+
+
+def serial_sample(gen, x0: int, positions):
+    pos = np.ascontiguousarray(np.asarray(positions, dtype=np.uint64))
+    out = np.zeros(pos.shape[0], dtype=np.uint32)
+    rc = lib().orc_serial_sample(gen_id(gen), x0, pos.ctypes.data, pos.shape[0],
+                                 out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle serial_sample rejected its arguments")
+    return out
+
+
+def serial_fill(gen, x0: int, n: int):
+    out = np.zeros(n, dtype=np.uint32)
+    rc = lib().orc_serial_fill(gen_id(gen), x0, n, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle serial_fill rejected its arguments")
+    return out
+
+
+def checksum_draws(gen, seed: int, stream: int, n: int, *, luxury: int = 0) -> int:
+    return int(lib().orc_checksum_draws(gen_id(gen), luxury, seed, stream, n))
+
+
+def ranecu_components(s1: int, s2: int, n: int):
+    """The two MLCG components of RANECU, stepped separately."""
+    L = lib()
+    a, b = ctypes.c_int32(s1), ctypes.c_int32(s2)
+    c1 = np.array([L.orc_ranecu_comp1(ctypes.byref(a)) for _ in range(n)], dtype=np.uint32)
+    c2 = np.array([L.orc_ranecu_comp2(ctypes.byref(b)) for _ in range(n)], dtype=np.uint32)
+    return c1, c2

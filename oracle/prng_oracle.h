@@ -1,0 +1,128 @@
+/*
+ * prng_oracle.h -- reference oracle for the six uniform generators of
+ * V. Demchik, "Pseudo-random number generators for Monte Carlo simulations
+ * on Graphics Processing Units" (arXiv:1003.1898).
+ *
+ * TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY.  Plain, slow, single-threaded
+ * C written from the paper's definitions.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg load it.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * Conventions
+ *   - A generator "draw" is one delivered output.  Draw n is 1-based: the
+ *     first value returned after seeding is draw 1.
+ *   - u32 outputs: GGL x_n in [1, 2^31-2]; XOR128 the new word w; RANECU the
+ *     combined z in [1, 2147483562]; RANMAR and RANLUX the 24-bit integer
+ *     (the paper's float value times 2^24); MT19937 the tempered word.
+ *   - f32 outputs are (v >> sh) * 2^-24 computed exactly, with sh = 7 for
+ *     GGL/RANECU, 8 for XOR128/MT19937 and 0 for RANMAR/RANLUX.
+ *
+ * Parity pins live in tests/test_oracle_pins.py.  Two parts are only partly
+ * pinned ("parity unpinned"): the RANECU combination step (each component is
+ * pinned, the combination only by construction) and XOR128 (no printed known
+ * answer; pinned by the paper's GF(2) matrix form and by linearity).
+ */
+#ifndef PRNG_ORACLE_H
+#define PRNG_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Generator ids used by this oracle (its own numbering). */
+enum { ORC_GGL = 0, ORC_XOR128 = 1, ORC_RANECU = 2, ORC_RANMAR = 3,
+       ORC_RANLUX = 4, ORC_MT19937 = 5, ORC_NGEN = 6 };
+
+typedef struct { uint32_t x; } orc_ggl;
+typedef struct { uint32_t x, y, z, w; } orc_xor128;
+typedef struct { int32_t s1, s2; } orc_ranecu;
+typedef struct { int32_t u[98]; int32_t c; int32_t i97, j97; } orc_ranmar;
+typedef struct { int32_t x[24]; int32_t k; int32_t carry; int32_t p; int32_t pos; } orc_ranlux;
+typedef struct { uint32_t mt[624]; int32_t mti; } orc_mt;
+
+/* One stream of any generator. */
+typedef struct {
+  int32_t gen;
+  union { orc_ggl g; orc_xor128 x; orc_ranecu e; orc_ranmar m; orc_ranlux l; orc_mt t; } s;
+} orc_stream;
+
+/* SplitMix64 (Steele, Lea, Flood 2014): first output of a SplitMix64
+ * generator whose state is x. */
+uint64_t orc_splitmix64(uint64_t x);
+
+/* Per-generator initialisation from explicit seeds. */
+void orc_ggl_init(orc_ggl *s, uint32_t x0);
+void orc_xor128_init(orc_xor128 *s, uint32_t x, uint32_t y, uint32_t z, uint32_t w);
+void orc_ranecu_init(orc_ranecu *s, int32_t s1, int32_t s2);
+void orc_rmarin(orc_ranmar *s, int32_t ij, int32_t kl);
+void orc_ranlux_init(orc_ranlux *s, uint32_t seed, int32_t p);
+void orc_mt_init(orc_mt *s, uint32_t seed);
+
+/* One draw. */
+uint32_t orc_ggl_next(orc_ggl *s);
+uint32_t orc_xor128_next(orc_xor128 *s);
+uint32_t orc_ranecu_next(orc_ranecu *s);
+uint32_t orc_ranecu_comp1(int32_t *s1);   /* first MLCG component alone */
+uint32_t orc_ranecu_comp2(int32_t *s2);   /* second MLCG component alone */
+uint32_t orc_ranmar_next(orc_ranmar *s);
+uint32_t orc_swb_step(orc_ranlux *s);     /* one RCARRY core step, no decimation */
+uint32_t orc_ranlux_next(orc_ranlux *s);
+uint32_t orc_mt_next(orc_mt *s);
+
+/* Luxury level 0..4 or p in {24,48,97,223,389} -> p; -1 if invalid. */
+int32_t orc_luxury_p(int32_t luxury);
+
+/* Exact float conversion of a u32 output of generator gen. */
+float orc_to_f32(int32_t gen, uint32_t v);
+
+/* Seed stream i of a handle created with base seed `seed`:
+ * s = splitmix64(seed + i), then the per-generator map.  Returns 0 or -1. */
+int orc_stream_seed(orc_stream *st, int32_t gen, int32_t luxury, uint64_t seed, uint64_t i);
+uint32_t orc_stream_next(orc_stream *st);
+
+/* Streams [stream0, stream0+n_streams) of a handle (gen, luxury, seed): each
+ * stream first discards `skip` draws, then writes n_per draws, stream-major.
+ * Either output pointer may be NULL.  Returns 0 or -1. */
+int orc_fill(int32_t gen, int32_t luxury, uint64_t seed, uint64_t stream0,
+             uint32_t n_streams, uint64_t skip, uint64_t n_per,
+             uint32_t *out_u32, float *out_f32);
+
+/* Draws at sorted 0-based positions pos[0..n_pos) of one stream. */
+int orc_sample(int32_t gen, int32_t luxury, uint64_t seed, uint64_t stream,
+               const uint64_t *pos, uint64_t n_pos, uint32_t *out_u32);
+
+/* n draws of a stream initialised from explicit seeds instead of the
+ * splitmix64 map: GGL {x0}; XOR128 {x,y,z,w}; RANECU {s1,s2}; RANMAR
+ * {ij,kl}; RANLUX {seed} with the given luxury; MT19937 {seed}.
+ * Returns 0 or -1. */
+int orc_explicit_draws(int32_t gen, int32_t luxury, const uint64_t *seeds,
+                       uint32_t n_seeds, uint64_t n, uint32_t *out_u32);
+
+/* Modular exponentiation a^e mod m by square-and-multiply (m < 2^32). */
+uint64_t orc_modpow(uint64_t a, uint64_t e, uint64_t m);
+
+/* Jump-ahead of the multiplicative congruential generators:
+ * x_{n+k} = (a^k mod m) x_n mod m, applied to GGL and to each RANECU
+ * component separately. */
+uint32_t orc_ggl_jump(uint32_t x, uint64_t k);
+void orc_ranecu_jump(orc_ranecu *s, uint64_t k);
+
+/* The single serial sequence started at x0 (GGL: x0 = seed value; RANECU:
+ * x0 = s1 | s2 << 32): out[j] = draw j+1.  Returns the draws at sorted
+ * 0-based positions pos[0..n_pos) by stepping serially. */
+int orc_serial_sample(int32_t gen, uint64_t x0, const uint64_t *pos,
+                      uint64_t n_pos, uint32_t *out_u32);
+/* Same sequence, the first n draws, written in full. */
+int orc_serial_fill(int32_t gen, uint64_t x0, uint64_t n, uint32_t *out_u32);
+
+/* Timing helper for the CPU baseline: draws n values from one stream and
+ * returns a running checksum so the work cannot be optimised away. */
+uint64_t orc_checksum_draws(int32_t gen, int32_t luxury, uint64_t seed,
+                            uint64_t stream, uint64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
