@@ -1,0 +1,421 @@
+"""Benchmark of the bulk-generation hot path on GB300.
+
+One step = one pass of the whole path over the roofline workload:
+  * re-seed every stream of the six handles on the device;
+  * GGL, XOR128, RANECU, RANMAR, RANLUX (p = 24) fill 2^30 u32 and 2^30 f32
+    each over 131,072 streams (8,192 per stream); MT19937 the same over
+    8,192 streams (131,072 per stream);
+  * GGL and RANECU jump-ahead fill 2^30 draws of one sequence from x0 = 1
+    in 65,536 chunks.
+value = random numbers written per second (whole job, all ranks).  Outputs
+(4 GiB per buffer) are far larger than L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the paper's plain single-threaded
+definitions) on this machine's host cores on a bounded sample of the same
+workload mix.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GENS = ("ggl", "xor128", "ranecu", "ranmar", "ranlux", "mt19937")
+N_STREAMS = 131072
+N_PER = 8192
+MT_STREAMS = 8192
+MT_PER = 131072
+JUMP_N = 2**30
+JUMP_CHUNKS = 65536
+JUMP_X0 = {"ggl": 1, "ranecu": 1 | (1 << 32)}
+SEED = 0x5EED
+RANLUX_P = 24
+STATE_WORDS = {"ggl": 1, "xor128": 4, "ranecu": 2, "ranmar": 98, "ranlux": 25, "mt19937": 624}
+METRIC = "random numbers/s per generator (and % of HBM-write roofline); batched p50/p99 latency"
+WORKLOAD = ("roofline bulk fill: GGL, XOR128, RANECU, RANMAR, RANLUX p=24 each 2^30 u32 + 2^30 f32 "
+            "over 131072 streams; MT19937 2^30 u32 + 2^30 f32 over 8192 streams; GGL and RANECU "
+            "jump-ahead 2^30 draws from x0=1 in 65536 chunks; streams re-seeded each step")
+
+
+def shape(gen):
+    return (MT_STREAMS, MT_PER) if gen == "mt19937" else (N_STREAMS, N_PER)
+
+
+def step_items():
+    """(label, generator, kind, numbers) for one step, in launch order."""
+    items = []
+    for g in GENS:
+        ns, nper = shape(g)
+        items.append((f"{g}_u32", g, "u32", ns * nper))
+        items.append((f"{g}_f32", g, "f32", ns * nper))
+    for g in ("ggl", "ranecu"):
+        items.append((f"{g}_jump", g, "jump", JUMP_N))
+    return items
+
+
+def numbers_per_step():
+    return sum(n for _, _, _, n in step_items())
+
+
+def algorithmic_bytes(label, gen, kind, numbers):
+    """Bytes a launch must move: 4 B per output plus one read and one write
+    of the stream state (a jump chunk's state is computed, not loaded)."""
+    if kind == "jump":
+        return 4 * numbers
+    ns, _ = shape(gen)
+    return 4 * numbers + 2 * 4 * STATE_WORDS[gen] * ns
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1003_1898_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(label):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        if t.get("sources") != kernel_sources_hash():
+            return None
+        return t["per_launch_bytes"].get(label)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def cpu_oracle_rate(sample_per_item: int):
+    """Oracle (single thread) numbers/s on the step's mix: each item draws
+    `sample_per_item` numbers; the mix rate is total numbers / total time,
+    with every item weighted by its share of the step."""
+    import oracle
+    oracle.lib()
+    t_total = 0.0
+    n_total = 0
+    for label, g, kind, numbers in step_items():
+        t0 = time.perf_counter()
+        if kind == "jump":
+            oracle.serial_fill(g, JUMP_X0[g], sample_per_item)
+        else:
+            lux = RANLUX_P if g == "ranlux" else 0
+            # u32 and f32 share the integer draws; f32 adds one exact conversion
+            if kind == "f32":
+                u, f = oracle.fill(g, SEED, 1, sample_per_item, luxury=lux, want_f32=True)
+            else:
+                oracle.checksum_draws(g, SEED, 0, sample_per_item, luxury=lux)
+        dt = time.perf_counter() - t0
+        t_total += dt * (numbers / sample_per_item)
+        n_total += numbers
+    return n_total / t_total, t_total
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sample = args.cpu_sample
+    steps_t = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, _ = cpu_oracle_rate(sample)
+        if i >= args.warmup:
+            steps_t.append((time.perf_counter() - t0, rate))
+    rate = statistics.median(r for _, r in steps_t)
+    ms = 1e3 * numbers_per_step() / rate
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "numbers/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": rate, "unit": "numbers/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} draws per step item, single thread, scaled to "
+                                   "the step's mix"},
+        "e2e": {"value": rate, "unit": "numbers/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1003_1898_gb300 as P
+    from paper_1003_1898_gb300 import build as B
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    P.lib()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+
+    # Each rank owns disjoint streams: seed bases offset by the stream count.
+    seed_r = {g: SEED + rank * shape(g)[0] for g in GENS}
+    handles = {g: P.prng_create(g, seed_r[g], shape(g)[0], RANLUX_P if g == "ranlux" else 0)
+               for g in GENS}
+    out_u = torch.empty(N_STREAMS * N_PER, dtype=torch.int32, device=dev)
+    out_f = torch.empty(N_STREAMS * N_PER, dtype=torch.float32, device=dev)
+    items = step_items()
+    ev = {lab: [] for lab, *_ in items}
+
+    def one_step(record):
+        for g in GENS:
+            P.prng_reseed(handles[g], seed_r[g], sid)
+        for lab, g, kind, numbers in items:
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            if kind == "u32":
+                P.prng_fill_u32(handles[g], out_u.data_ptr(), shape(g)[1], sid)
+            elif kind == "f32":
+                P.prng_fill_f32(handles[g], out_f.data_ptr(), shape(g)[1], sid)
+            else:
+                P.prng_fill_jump_u32(g, JUMP_X0[g], JUMP_N, JUMP_CHUNKS, out_u.data_ptr(), sid)
+            if record:
+                e1.record(stream)
+                ev[lab].append((e0, e1))
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            one_step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * numbers_per_step() / (ms_step / 1e3)
+    launches_per_step = len(GENS) + len(items)
+
+    # per-item device time (events on the launching stream) and roofline
+    hbm, peak_kind = peaks()
+    per = {}
+    for lab, g, kind, numbers in items:
+        ts = [a.elapsed_time(b) for a, b in ev[lab]]
+        ms = statistics.mean(ts)
+        byt = algorithmic_bytes(lab, g, kind, numbers)
+        per[lab] = {"ms": ms, "numbers_per_s": numbers / (ms / 1e3),
+                    "gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
+    dom = max(items, key=lambda it: per[it[0]]["ms"])
+    dl = dom[0]
+    roof = {"kernel": dl, "bound": "hbm", "achieved": per[dl]["gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": per[dl]["frac_hbm"], "traffic": recorded_traffic(dl),
+            "peak_source": f"{peak_kind} hbm_gbs (copy, read+write)",
+            "algorithmic_bytes_per_launch": algorithmic_bytes(*dom)}
+
+    # end-to-end through the public API with host buffers: fill, then copy
+    # every output to pinned host memory inside the timed region.
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(P, handles, seed_r, items, dev, args)
+
+    for h in handles.values():
+        P.prng_destroy(h)
+    del out_u, out_f
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, secs = cpu_oracle_rate(args.cpu_sample)
+        cpu = {"value": rate, "unit": "numbers/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} draws per step item ({len(items)} items), single "
+                         f"thread, weighted by the step's mix"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "numbers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "numbers_per_step_per_gpu": numbers_per_step(),
+                   "l2": "outputs (4 GiB per buffer) larger than L2; no flush",
+                   "parallelism": f"{world} independent partitions of the streams"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "per_kernel": per,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_e2e(P, handles, seed_r, items, dev, args):
+    import torch
+    stream = torch.cuda.current_stream()
+    copy_stream = torch.cuda.Stream(device=dev)
+    nbuf = 2
+    bufs = [torch.empty(N_STREAMS * N_PER, dtype=torch.int32, device=dev) for _ in range(nbuf)]
+    host = torch.empty(N_STREAMS * N_PER, dtype=torch.int32, pin_memory=True)
+    done = [torch.cuda.Event() for _ in range(nbuf)]
+    d2h = 0
+    steps = max(1, min(args.steps, 2))
+
+    def one():
+        nonlocal d2h
+        for g in GENS:
+            P.prng_reseed(handles[g], seed_r[g], stream.cuda_stream)
+        for i, (lab, g, kind, numbers) in enumerate(items):
+            b = bufs[i % nbuf]
+            stream.wait_event(done[i % nbuf])
+            if kind == "u32":
+                P.prng_fill_u32(handles[g], b.data_ptr(), shape(g)[1], stream.cuda_stream)
+            elif kind == "f32":
+                P.prng_fill_f32(handles[g], b.data_ptr(), shape(g)[1], stream.cuda_stream)
+            else:
+                P.prng_fill_jump_u32(g, JUMP_X0[g], JUMP_N, JUMP_CHUNKS, b.data_ptr(),
+                                     stream.cuda_stream)
+            filled = torch.cuda.Event()
+            filled.record(stream)
+            copy_stream.wait_event(filled)
+            with torch.cuda.stream(copy_stream):
+                host.copy_(b[:numbers], non_blocking=True) if numbers == host.numel() else \
+                    host[:numbers].copy_(b[:numbers], non_blocking=True)
+            done[i % nbuf].record(copy_stream)
+            d2h += 4 * numbers
+
+    one()
+    torch.cuda.synchronize()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": numbers_per_step() / dt, "unit": "numbers/s",
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // steps,
+            "note": "fills through the C ABI, every output copied to pinned host memory on a "
+                    "second stream; inputs are scalar seeds passed by value"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=2**26)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,130 @@
+/*
+ * prng.h -- C ABI of libprng, a GB300 (sm_103a) library for bulk uniform
+ * pseudo-random numbers from the six generators of V. Demchik,
+ * "Pseudo-random number generators for Monte Carlo simulations on GPUs"
+ * (arXiv:1003.1898): GGL (Section 3.2), XOR128 (Section 3.3), RANECU
+ * (Section 3.4), RANMAR (Section 3.5), RANLUX (Section 3.6) and MT19937
+ * (Section 3.7), with the recurrences of Appendix A.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative PRNG_E* code otherwise
+ *     (prng_strerror() names it).  Arguments are validated on the host
+ *     before anything is launched; a rejected call changes nothing.
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *     library never frees them.  Host pointers are named h_*.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Fills are asynchronous on that stream; the caller orders
+ *     work on one handle (a handle is not thread-safe).
+ *   - Outputs are stream-major: element (i, j) of a fill, the j-th new draw
+ *     of stream i, is at d_out[i * n_per_stream + j].
+ *   - u32 outputs: GGL x_n in [1, 2^31-2]; XOR128 the new word; RANECU the
+ *     combined value in [1, 2147483562]; RANMAR and RANLUX the 24-bit
+ *     integer (the paper's float value times 2^24); MT19937 the tempered
+ *     word.  f32 outputs are the exact scaling (v >> sh) * 2^-24 in [0, 1),
+ *     sh = 7 (GGL, RANECU), 8 (XOR128, MT19937), 0 (RANMAR, RANLUX).
+ */
+#ifndef PRNG_H
+#define PRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum prng_gen {
+  PRNG_GGL = 0,      /* x <- 16807 x mod (2^31 - 1)                       (Section 3.2) */
+  PRNG_XOR128 = 1,   /* Marsaglia xorshift, shifts 11/19/8                 (Section 3.3) */
+  PRNG_RANECU = 2,   /* L'Ecuyer combination of two MLCGs                  (Section 3.4) */
+  PRNG_RANMAR = 3,   /* LFG(97,33,-) mod 2^24 combined with a Weyl sequence (Section 3.5) */
+  PRNG_RANLUX = 4,   /* RCARRY SWB(2^24,10,24) with luxury decimation      (Section 3.6) */
+  PRNG_MT19937 = 5   /* Mersenne twister                                   (Section 3.7) */
+} prng_gen_t;
+
+enum {
+  PRNG_OK = 0,
+  PRNG_EGEN = -1,        /* unknown generator                                   */
+  PRNG_ELUXURY = -2,     /* RANLUX luxury not in {0..4, 24, 48, 97, 223, 389}    */
+  PRNG_ESIZE = -3,       /* zero streams/chunks, or a size that overflows        */
+  PRNG_ENULL = -4,       /* a required pointer is NULL                           */
+  PRNG_EALLOC = -5,      /* device allocation failed                             */
+  PRNG_ECUDA = -6,       /* a CUDA call or launch failed                         */
+  PRNG_EUNSUPPORTED = -7,/* operation not defined for this generator             */
+  PRNG_EBLOB = -8,       /* malformed or mismatched state blob                   */
+  PRNG_ESEED = -9        /* jump start value outside the generator's range       */
+};
+
+/* Opaque handle: one generator type, n_streams independent streams, their
+ * state resident in device memory owned by the handle. */
+typedef struct prng_state prng_state;
+
+/* Create a handle with n_streams streams of generator `gen` on the current
+ * CUDA device and seed them on the device (one launch, then a synchronise).
+ * Stream i is seeded from s = splitmix64(seed + i) (SplitMix64 of Steele,
+ * Lea and Flood: add 0x9E3779B97F4A7C15, then its mix64 finaliser), mapped
+ * into the generator's seed range:
+ *   GGL x0 = 1 + s mod (2^31-2); XOR128 (x,y,z,w) = the 32-bit halves of s and
+ *   of splitmix64(s) (w = 1 if all are 0); RANECU s1 = 1 + lo32(s) mod
+ *   (m1-1), s2 = 1 + hi32(s) mod (m2-1); RANMAR RMARIN(ij = lo32(s) mod
+ *   31329, kl = hi32(s) mod 30082) (Section 3.5); RANLUX table from the MLCG
+ *   40014 mod 2147483563 started at s mod 2147483563 (19780503 if 0);
+ *   MT19937 init_genrand(lo32(s)).
+ * `luxury` selects RANLUX's p (levels 0..4 or p in {24,48,97,223,389},
+ * Appendix A "RANLUX"); it is ignored for the other generators.
+ * On success *out owns device memory until prng_destroy(). */
+int prng_create(prng_state **out, prng_gen_t gen, uint64_t seed, uint32_t n_streams,
+                uint32_t luxury);
+
+/* Re-seed every stream of an existing handle in place, as prng_create would
+ * with `seed`; asynchronous on `stream`, allocates nothing. */
+int prng_reseed(prng_state *st, uint64_t seed, void *stream);
+
+/* Write the next n_per_stream draws of every stream to d_out (stream-major,
+ * n_streams * n_per_stream elements) and advance every stream by
+ * n_per_stream.  n_per_stream = 0 is a no-op.  d_out needs 4-byte alignment;
+ * 16-byte alignment with n_per_stream % 4 == 0 takes the vector-store path. */
+int prng_fill_u32(prng_state *st, uint32_t *d_out, uint64_t n_per_stream, void *stream);
+int prng_fill_f32(prng_state *st, float *d_out, uint64_t n_per_stream, void *stream);
+
+/* Advance every stream by k draws without writing them (same result as a
+ * fill of k whose output is thrown away).  GGL and RANECU jump in O(log k)
+ * by a^k mod m (Appendix A, eq. MLCG); the others step. */
+int prng_skip(prng_state *st, uint64_t k, void *stream);
+
+/* Checkpoint.  prng_get_state copies the handle's full state into h_buf
+ * (host memory, *bytes long); with h_buf == NULL it only stores the size
+ * needed in *bytes.  It synchronises the device.  prng_set_state restores
+ * a blob taken from a handle of the same generator, luxury and n_streams
+ * (PRNG_EBLOB otherwise).  Blob layout: 8 uint32 header words {magic
+ * 0x50524E47, version 1, gen, p, n_streams, words_per_stream, position,
+ * 0} followed by n_streams * words_per_stream uint32 words, stream-major. */
+int prng_get_state(prng_state *st, void *h_buf, size_t *bytes);
+int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
+
+/* Single-sequence jump-ahead fill (GGL and RANECU only): write draws 1..n of
+ * the one sequence started at x0 to d_out[0..n), computed as n_chunks
+ * contiguous chunks in parallel, chunk c starting from a^(c*L) x0 mod m,
+ * L = ceil(n / n_chunks), by square-and-multiply (Appendix A, eq. MLCG).
+ * GGL: x0 in [1, 2^31-2].  RANECU: x0 = s1 | (s2 << 32) with s1 in
+ * [1, m1-1], s2 in [1, m2-1], both components jumped separately.  Other
+ * generators return PRNG_EUNSUPPORTED. */
+int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
+                       uint32_t *d_out, void *stream);
+int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
+                       float *d_out, void *stream);
+
+/* Handle properties (any pointer may be NULL). */
+int prng_info(const prng_state *st, int32_t *gen, int32_t *p, uint32_t *n_streams,
+              uint64_t *state_bytes);
+
+/* Release the handle's device memory.  NULL is accepted. */
+void prng_destroy(prng_state *st);
+
+/* Static English text for an error code. */
+const char *prng_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRNG_H */

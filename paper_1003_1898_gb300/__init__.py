@@ -1,0 +1,200 @@
+"""paper_1003_1898_gb300 -- Python binding of libprng (GB300 uniform PRNGs).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name in ``libprng.so`` (declared in ``include/prng.h``); every draw
+is produced by the library's CUDA kernels.  PyTorch is used for device
+memory and the current CUDA stream.  If the shared library has not been
+built, ``lib()`` raises -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libprng.so")
+
+GGL, XOR128, RANECU, RANMAR, RANLUX, MT19937 = range(6)
+GEN_NAMES = ("ggl", "xor128", "ranecu", "ranmar", "ranlux", "mt19937")
+GEN_IDS = {n: i for i, n in enumerate(GEN_NAMES)}
+LUXURY_P = (24, 48, 97, 223, 389)
+STATE_WORDS = (1, 4, 2, 98, 25, 624)
+
+_lib = None
+
+
+class PrngError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {prng_strerror(code)} (code {code})")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libprng.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libprng.so is not built ({LIB_PATH}); run "
+                           "paper_1003_1898_gb300.build.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+    sig = {
+        "prng_create": ([ctypes.POINTER(vp), ctypes.c_int, u64, u32, u32], ctypes.c_int),
+        "prng_reseed": ([vp, u64, vp], ctypes.c_int),
+        "prng_fill_u32": ([vp, vp, u64, vp], ctypes.c_int),
+        "prng_fill_f32": ([vp, vp, u64, vp], ctypes.c_int),
+        "prng_skip": ([vp, u64, vp], ctypes.c_int),
+        "prng_get_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "prng_set_state": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
+        "prng_fill_jump_u32": ([ctypes.c_int, u64, u64, u32, vp, vp], ctypes.c_int),
+        "prng_fill_jump_f32": ([ctypes.c_int, u64, u64, u32, vp, vp], ctypes.c_int),
+        "prng_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u32),
+                       ctypes.POINTER(u64)], ctypes.c_int),
+        "prng_destroy": ([vp], None),
+        "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _gen(gen) -> int:
+    return GEN_IDS[gen] if isinstance(gen, str) else int(gen)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()   # torch tensor
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise PrngError(rc, what)
+
+
+def prng_strerror(code: int) -> str:
+    return lib().prng_strerror(code).decode()
+
+
+def prng_create(gen, seed: int, n_streams: int, luxury: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().prng_create(ctypes.byref(h), _gen(gen), seed & (2**64 - 1), n_streams, luxury),
+           "prng_create")
+    return h
+
+
+def prng_reseed(h, seed: int, stream=None):
+    _check(lib().prng_reseed(h, seed & (2**64 - 1), _stream(stream)), "prng_reseed")
+
+
+def prng_fill_u32(h, out, n_per_stream: int, stream=None):
+    _check(lib().prng_fill_u32(h, _ptr(out), n_per_stream, _stream(stream)), "prng_fill_u32")
+
+
+def prng_fill_f32(h, out, n_per_stream: int, stream=None):
+    _check(lib().prng_fill_f32(h, _ptr(out), n_per_stream, _stream(stream)), "prng_fill_f32")
+
+
+def prng_skip(h, k: int, stream=None):
+    _check(lib().prng_skip(h, k, _stream(stream)), "prng_skip")
+
+
+def prng_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().prng_get_state(h, None, ctypes.byref(n)), "prng_get_state")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().prng_get_state(h, buf, ctypes.byref(n)), "prng_get_state")
+    return buf.raw[:n.value]
+
+
+def prng_set_state(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().prng_set_state(h, buf, len(blob)), "prng_set_state")
+
+
+def prng_fill_jump_u32(gen, x0: int, n: int, n_chunks: int, out, stream=None):
+    _check(lib().prng_fill_jump_u32(_gen(gen), x0, n, n_chunks, _ptr(out), _stream(stream)),
+           "prng_fill_jump_u32")
+
+
+def prng_fill_jump_f32(gen, x0: int, n: int, n_chunks: int, out, stream=None):
+    _check(lib().prng_fill_jump_f32(_gen(gen), x0, n, n_chunks, _ptr(out), _stream(stream)),
+           "prng_fill_jump_f32")
+
+
+def prng_info(h) -> dict:
+    g, p = ctypes.c_int32(), ctypes.c_int32()
+    n, b = ctypes.c_uint32(), ctypes.c_uint64()
+    _check(lib().prng_info(h, ctypes.byref(g), ctypes.byref(p), ctypes.byref(n), ctypes.byref(b)),
+           "prng_info")
+    return {"gen": g.value, "p": p.value, "n_streams": n.value, "state_bytes": b.value}
+
+
+def prng_destroy(h):
+    lib().prng_destroy(h)
+
+
+class Generator:
+    """A handle of n_streams streams of one generator, owned by this object."""
+
+    def __init__(self, gen, seed: int, n_streams: int, luxury: int = 0):
+        self.gen = _gen(gen)
+        self.n_streams = n_streams
+        self.luxury = luxury
+        self._h = prng_create(self.gen, seed, n_streams, luxury)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def fill(self, n_per_stream: int, dtype: str = "u32", out=None, stream=None):
+        """Next n_per_stream draws of every stream as a (n_streams, n_per_stream)
+        CUDA tensor (int32 holding the u32 bits, or float32)."""
+        import torch
+        if out is None:
+            tdt = torch.float32 if dtype == "f32" else torch.int32
+            out = torch.empty((self.n_streams, n_per_stream), dtype=tdt, device="cuda")
+        if dtype == "f32":
+            prng_fill_f32(self._h, out, n_per_stream, stream)
+        else:
+            prng_fill_u32(self._h, out, n_per_stream, stream)
+        return out
+
+    def skip(self, k: int, stream=None):
+        prng_skip(self._h, k, stream)
+
+    def reseed(self, seed: int, stream=None):
+        prng_reseed(self._h, seed, stream)
+
+    def get_state(self) -> bytes:
+        return prng_get_state(self._h)
+
+    def set_state(self, blob: bytes):
+        prng_set_state(self._h, blob)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            prng_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,316 @@
+// abi.cu -- the exported C ABI of libprng (declared in include/prng.h).
+//
+// Host side only: argument validation, device allocation of stream state,
+// bookkeeping of the positions that are uniform over a handle's streams
+// (RANLUX's place in its luxury block, MT19937's table index), and dispatch
+// to the kernels.  Every draw is produced on the GPU.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/prng.h"
+#include "common.cuh"
+
+using namespace prng;
+
+struct prng_state {
+  int gen;
+  int p;                 // RANLUX luxury p (0 for the others)
+  uint64_t n_streams;
+  uint32_t* d_state;     // device state, layout in common.cuh
+  uint32_t pos;          // RANLUX: draws delivered from the open block; MT: mti
+  int device;
+};
+
+namespace {
+
+constexpr uint32_t kBlobMagic = 0x50524E47u;  // "PRNG"
+constexpr uint32_t kBlobVersion = 1u;
+
+int luxury_to_p(uint32_t luxury) {
+  static const int P[5] = {24, 48, 97, 223, 389};
+  if (luxury <= 4) return P[luxury];
+  for (int i = 0; i < 5; i++)
+    if ((int)luxury == P[i]) return P[i];
+  return -1;
+}
+
+uint32_t initial_pos(int gen) { return gen == MT19937 ? 624u : 0u; }
+
+// Position after n more draws (all streams move together).
+uint32_t advance_pos(int gen, uint32_t pos, uint64_t n) {
+  if (n == 0) return pos;
+  if (gen == RANLUX) {
+    const uint64_t h = pos < 24 ? (24 - pos < n ? 24 - pos : n) : 0;
+    const uint64_t r = n - h;
+    return r == 0 ? (uint32_t)(pos + h) : (uint32_t)((r - 1) % 24 + 1);
+  }
+  if (gen == MT19937) {
+    const uint64_t h = pos < 624 ? (624 - pos < n ? 624 - pos : n) : 0;
+    const uint64_t r = n - h;
+    return r == 0 ? (uint32_t)(pos + h) : (uint32_t)((r - 1) % 624 + 1);
+  }
+  return 0;
+}
+
+int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t s) {
+  if (st == nullptr) return PRNG_ENULL;
+  if (n_per == 0) return PRNG_OK;
+  if (d_out == nullptr) return PRNG_ENULL;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
+  if (st->n_streams > UINT64_MAX / n_per) return PRNG_ESIZE;
+  FillDesc d{};
+  d.state = st->d_state;
+  d.n_rows = st->n_streams;
+  d.n_per = n_per;
+  d.out = d_out;
+  d.pitch = n_per;
+  d.limit = UINT64_MAX;
+  d.pos = st->pos;
+  d.p = st->p;
+  d.f32 = f32;
+  d.jump = 0;
+  const Tile t = default_tile(st->gen, st->p);
+  cudaError_t e;
+  switch (st->gen) {
+    case RANMAR: e = launch_fill_ranmar(d, t, s); break;
+    case RANLUX: e = launch_fill_ranlux(d, t, s); break;
+    case MT19937: e = launch_fill_mt(d, t, s); break;
+    default: e = launch_fill_simple(st->gen, d, t, s); break;
+  }
+  if (e != cudaSuccess) return PRNG_ECUDA;
+  st->pos = advance_pos(st->gen, st->pos, n_per);
+  return PRNG_OK;
+}
+
+int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
+              cudaStream_t s) {
+  if (gen < 0 || gen > 5) return PRNG_EGEN;
+  if (gen != GGL && gen != RANECU) return PRNG_EUNSUPPORTED;
+  if (n == 0) return PRNG_OK;
+  if (d_out == nullptr) return PRNG_ENULL;
+  if (n_chunks == 0) return PRNG_ESIZE;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
+  if (gen == GGL) {
+    if (x0 == 0 || x0 >= 2147483647ull) return PRNG_ESEED;
+  } else {
+    const uint64_t s1 = x0 & 0xFFFFFFFFull, s2 = x0 >> 32;
+    if (s1 == 0 || s1 >= 2147483563ull || s2 == 0 || s2 >= 2147483399ull) return PRNG_ESEED;
+  }
+  const uint64_t L = (n + n_chunks - 1) / n_chunks;  // draws per chunk
+  FillDesc d{};
+  d.state = nullptr;
+  d.n_rows = (n + L - 1) / L;                        // no empty chunk
+  d.n_per = L;
+  d.out = d_out;
+  d.pitch = L;
+  d.limit = n;
+  d.x0 = x0;
+  d.f32 = f32;
+  d.jump = 1;
+  if (launch_fill_simple(gen, d, default_tile(gen, 0), s) != cudaSuccess) return PRNG_ECUDA;
+  return PRNG_OK;
+}
+
+}  // namespace
+
+namespace prng {
+
+Tile default_tile(int gen, int p) {
+  (void)p;
+  switch (gen) {
+    case RANMAR: return Tile{64, 97};
+    case RANLUX: return Tile{128, 48};
+    case MT19937: return Tile{128, 624};
+    default: return Tile{128, 32};
+  }
+}
+
+}  // namespace prng
+
+extern "C" {
+
+int prng_create(prng_state** out, prng_gen_t gen, uint64_t seed, uint32_t n_streams,
+                uint32_t luxury) {
+  if (out == nullptr) return PRNG_ENULL;
+  *out = nullptr;
+  const int g = (int)gen;
+  if (g < 0 || g > 5) return PRNG_EGEN;
+  int p = 0;
+  if (g == RANLUX) {
+    p = luxury_to_p(luxury);
+    if (p < 0) return PRNG_ELUXURY;
+  }
+  if (n_streams == 0) return PRNG_ESIZE;
+  prng_state* st = new (std::nothrow) prng_state;
+  if (st == nullptr) return PRNG_EALLOC;
+  st->gen = g;
+  st->p = p;
+  st->n_streams = n_streams;
+  st->pos = initial_pos(g);
+  st->d_state = nullptr;
+  cudaGetDevice(&st->device);
+  const size_t bytes = (size_t)n_streams * kWords[g] * sizeof(uint32_t);
+  if (cudaMalloc(&st->d_state, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete st;
+    return PRNG_EALLOC;
+  }
+  if (launch_seed(g, p, seed, n_streams, st->d_state, 0) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess) {
+    cudaFree(st->d_state);
+    delete st;
+    return PRNG_ECUDA;
+  }
+  *out = st;
+  return PRNG_OK;
+}
+
+int prng_reseed(prng_state* st, uint64_t seed, void* stream) {
+  if (st == nullptr) return PRNG_ENULL;
+  if (launch_seed(st->gen, st->p, seed, st->n_streams, st->d_state,
+                  static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return PRNG_ECUDA;
+  st->pos = initial_pos(st->gen);
+  return PRNG_OK;
+}
+
+int prng_fill_u32(prng_state* st, uint32_t* d_out, uint64_t n_per_stream, void* stream) {
+  return fill_impl(st, d_out, n_per_stream, 0, static_cast<cudaStream_t>(stream));
+}
+
+int prng_fill_f32(prng_state* st, float* d_out, uint64_t n_per_stream, void* stream) {
+  return fill_impl(st, d_out, n_per_stream, 1, static_cast<cudaStream_t>(stream));
+}
+
+int prng_skip(prng_state* st, uint64_t k, void* stream) {
+  if (st == nullptr) return PRNG_ENULL;
+  if (k == 0) return PRNG_OK;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (st->gen == GGL || st->gen == RANECU) {
+    e = launch_skip_mlcg(st->gen, st->d_state, st->n_streams, k, s);
+  } else {
+    FillDesc d{};
+    d.state = st->d_state;
+    d.n_rows = st->n_streams;
+    d.n_per = k;
+    d.out = nullptr;
+    d.pitch = 0;
+    d.limit = 0;
+    d.pos = st->pos;
+    d.p = st->p;
+    const Tile t = default_tile(st->gen, st->p);
+    switch (st->gen) {
+      case RANMAR: e = launch_fill_ranmar(d, t, s); break;
+      case RANLUX: e = launch_fill_ranlux(d, t, s); break;
+      case MT19937: e = launch_fill_mt(d, t, s); break;
+      default: e = launch_fill_simple(st->gen, d, t, s); break;
+    }
+  }
+  if (e != cudaSuccess) return PRNG_ECUDA;
+  st->pos = advance_pos(st->gen, st->pos, k);
+  return PRNG_OK;
+}
+
+int prng_get_state(prng_state* st, void* h_buf, size_t* bytes) {
+  if (st == nullptr || bytes == nullptr) return PRNG_ENULL;
+  const uint64_t W = kWords[st->gen], n = st->n_streams;
+  const size_t need = (8 + (size_t)n * W) * sizeof(uint32_t);
+  if (h_buf == nullptr) {
+    *bytes = need;
+    return PRNG_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return PRNG_ESIZE;
+  }
+  std::vector<uint32_t> dev((size_t)n * W);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(dev.data(), st->d_state, dev.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PRNG_ECUDA;
+  uint32_t* b = static_cast<uint32_t*>(h_buf);
+  const uint32_t hdr[8] = {kBlobMagic, kBlobVersion, (uint32_t)st->gen, (uint32_t)st->p,
+                           (uint32_t)n, (uint32_t)W, st->pos, 0u};
+  std::memcpy(b, hdr, sizeof(hdr));
+  uint32_t* body = b + 8;
+  if (st->gen == MT19937) {
+    std::memcpy(body, dev.data(), dev.size() * 4);
+  } else {  // SoA on the device, stream-major in the blob
+    for (uint64_t i = 0; i < n; i++)
+      for (uint64_t w = 0; w < W; w++) body[i * W + w] = dev[w * n + i];
+  }
+  *bytes = need;
+  return PRNG_OK;
+}
+
+int prng_set_state(prng_state* st, const void* h_buf, size_t bytes) {
+  if (st == nullptr || h_buf == nullptr) return PRNG_ENULL;
+  const uint64_t W = kWords[st->gen], n = st->n_streams;
+  const size_t need = (8 + (size_t)n * W) * sizeof(uint32_t);
+  if (bytes != need) return PRNG_EBLOB;
+  const uint32_t* b = static_cast<const uint32_t*>(h_buf);
+  if (b[0] != kBlobMagic || b[1] != kBlobVersion || b[2] != (uint32_t)st->gen ||
+      b[3] != (uint32_t)st->p || b[4] != (uint32_t)n || b[5] != (uint32_t)W)
+    return PRNG_EBLOB;
+  const uint32_t pos = b[6];
+  if ((st->gen == RANLUX && pos > 24) || (st->gen == MT19937 && pos > 624)) return PRNG_EBLOB;
+  std::vector<uint32_t> dev((size_t)n * W);
+  const uint32_t* body = b + 8;
+  if (st->gen == MT19937) {
+    std::memcpy(dev.data(), body, dev.size() * 4);
+  } else {
+    for (uint64_t i = 0; i < n; i++)
+      for (uint64_t w = 0; w < W; w++) dev[w * n + i] = body[i * W + w];
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(st->d_state, dev.data(), dev.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PRNG_ECUDA;
+  st->pos = pos;
+  return PRNG_OK;
+}
+
+int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
+                       uint32_t* d_out, void* stream) {
+  return jump_impl((int)gen, x0, n, n_chunks, d_out, 0, static_cast<cudaStream_t>(stream));
+}
+
+int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
+                       float* d_out, void* stream) {
+  return jump_impl((int)gen, x0, n, n_chunks, d_out, 1, static_cast<cudaStream_t>(stream));
+}
+
+int prng_info(const prng_state* st, int32_t* gen, int32_t* p, uint32_t* n_streams,
+              uint64_t* state_bytes) {
+  if (st == nullptr) return PRNG_ENULL;
+  if (gen) *gen = st->gen;
+  if (p) *p = st->p;
+  if (n_streams) *n_streams = (uint32_t)st->n_streams;
+  if (state_bytes) *state_bytes = st->n_streams * (uint64_t)kWords[st->gen] * 4;
+  return PRNG_OK;
+}
+
+void prng_destroy(prng_state* st) {
+  if (st == nullptr) return;
+  if (st->d_state) cudaFree(st->d_state);
+  delete st;
+}
+
+const char* prng_strerror(int code) {
+  switch (code) {
+    case PRNG_OK: return "success";
+    case PRNG_EGEN: return "unknown generator";
+    case PRNG_ELUXURY: return "RANLUX luxury must be 0..4 or one of 24, 48, 97, 223, 389";
+    case PRNG_ESIZE: return "invalid size or alignment";
+    case PRNG_ENULL: return "required pointer is NULL";
+    case PRNG_EALLOC: return "device allocation failed";
+    case PRNG_ECUDA: return "CUDA call or kernel launch failed";
+    case PRNG_EUNSUPPORTED: return "operation not supported for this generator";
+    case PRNG_EBLOB: return "state blob does not match this handle";
+    case PRNG_ESEED: return "start value outside the generator's range";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

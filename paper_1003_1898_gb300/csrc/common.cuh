@@ -1,0 +1,134 @@
+// common.cuh -- internal definitions shared by the libprng kernels.
+//
+// Device-state layouts (all uint32 words):
+//   GGL      SoA [1][n]   x
+//   XOR128   SoA [4][n]   x, y, z, w
+//   RANECU   SoA [2][n]   s1, s2
+//   RANMAR   SoA [98][n]  V[0..96], C  -- V is the lag table in canonical order
+//                                         V[k] = U[i97 - k] (indices mod 97), so
+//                                         V[0] is the next entry overwritten and
+//                                         V[64] = U[j97] (Section 3.5; Appendix A,
+//                                         "RANMAR")
+//   RANLUX   SoA [25][n]  V[0..23], carry -- V[j] = x_{n-24+j}, oldest first
+//                                         (Appendix A, "AWC and SWB"); the
+//                                         position inside the luxury cycle is
+//                                         uniform over streams and lives in the
+//                                         handle
+//   MT19937  AoS [n][624] mt[0..623]     -- the read index mti is uniform over
+//                                         streams and lives in the handle
+// SoA keeps every per-thread state load/store coalesced; MT19937 is handled
+// one warp per stream, so its table is contiguous per stream instead.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace prng {
+
+enum Gen : int { GGL = 0, XOR128 = 1, RANECU = 2, RANMAR = 3, RANLUX = 4, MT19937 = 5 };
+
+constexpr int kWords[6] = {1, 4, 2, 98, 25, 624};
+
+// One fill (or skip, or jump fill) as the kernels see it.
+struct FillDesc {
+  uint32_t* state;     // device state (layout above); unused for jump fills
+  uint64_t n_rows;     // streams (or jump chunks)
+  uint64_t n_per;      // draws per row in this call
+  void* out;           // u32 or f32 output, NULL for a skip
+  uint64_t pitch;      // elements between consecutive rows of `out`
+  uint64_t limit;      // only elements with linear index < limit are written
+  uint64_t x0;         // jump fills: start value (RANECU: s1 | s2 << 32)
+  uint32_t pos;        // RANLUX: draws delivered from the current block; MT: mti
+  int32_t p;           // RANLUX luxury p
+  int32_t f32;         // 1: write floats
+  int32_t jump;        // 1: rows are chunks of one jump-ahead sequence
+};
+
+// Launch configuration of a fill kernel (chosen by the tuner or defaults).
+struct Tile {
+  int threads;   // threads per CTA (streams per CTA for thread-per-stream kernels)
+  int cols;      // staged columns per tile
+};
+
+cudaError_t launch_fill_simple(int gen, const FillDesc& d, Tile t, cudaStream_t s);
+cudaError_t launch_fill_ranmar(const FillDesc& d, Tile t, cudaStream_t s);
+cudaError_t launch_fill_ranlux(const FillDesc& d, Tile t, cudaStream_t s);
+cudaError_t launch_fill_mt(const FillDesc& d, Tile t, cudaStream_t s);
+cudaError_t launch_seed(int gen, int p, uint64_t seed, uint64_t n, uint32_t* state,
+                        cudaStream_t s);
+cudaError_t launch_skip_mlcg(int gen, uint32_t* state, uint64_t n, uint64_t k,
+                             cudaStream_t s);
+
+Tile default_tile(int gen, int p);
+
+// ------------------------------------------------------------------ device
+
+__device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// x <- A x mod (2^31 - C) for a multiplier A < 2^16 and a small C: the
+// 47-bit product is folded once with 2^31 = C (mod m), then one conditional
+// subtraction (unsigned min) brings it below m.  Same integer as the
+// paper's Schrage evaluation (Appendix A, eq. RANECU1), other route.
+template <uint32_t A, uint32_t C>
+__device__ __forceinline__ uint32_t mlcg_step(uint32_t x) {
+  constexpr uint32_t M = 0x80000000u - C;
+  const uint64_t p = (uint64_t)x * A;
+  const uint32_t r = ((uint32_t)p & 0x7FFFFFFFu) + (uint32_t)(p >> 31) * C;
+  return umin32(r, r - M);
+}
+
+// x y mod (2^31 - C) for arbitrary x, y < 2^31 (two folds).
+template <uint32_t C>
+__device__ __forceinline__ uint32_t mulmod_pm(uint32_t x, uint32_t y) {
+  constexpr uint32_t M = 0x80000000u - C;
+  const uint64_t p = (uint64_t)x * y;
+  const uint64_t t = (p & 0x7FFFFFFFull) + (p >> 31) * C;
+  const uint32_t r = (uint32_t)(t & 0x7FFFFFFFull) + (uint32_t)(t >> 31) * C;
+  return umin32(r, r - M);
+}
+
+// a^e mod (2^31 - C) by square-and-multiply.
+template <uint32_t C>
+__device__ __forceinline__ uint32_t powmod_pm(uint32_t a, uint64_t e) {
+  uint32_t r = 1, b = a;
+  while (e) {
+    if (e & 1) r = mulmod_pm<C>(r, b);
+    b = mulmod_pm<C>(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Exact float of a u32 draw: (v >> SH) < 2^24 converts exactly, and the
+// power-of-two scale is exact.
+template <int SH>
+__device__ __forceinline__ uint32_t as_f32_bits(uint32_t v) {
+  return __float_as_uint(__uint2float_rn(v >> SH) * 0x1p-24f);
+}
+
+// Streaming store: outputs are written once and never read back here.
+__device__ __forceinline__ void st_out(uint32_t* p, uint32_t v) { __stcs(p, v); }
+__device__ __forceinline__ void st_out4(uint32_t* p, uint4 v) {
+  __stcs(reinterpret_cast<uint4*>(p), v);
+}
+
+// Copy a staged tile (rows [0, T) of `tile`, row pitch SP words, columns
+// [0, w)) to out rows row0.. at columns g0..: warp wi takes rows wi, wi+NW,
+// ...; its lanes take consecutive columns, so each warp store is one
+// contiguous run of the row.
+template <int T>
+__device__ __forceinline__ void copy_rows_scalar(const uint32_t* tile, int sp, uint32_t* out,
+                                                 uint64_t gpitch, uint64_t row0, uint64_t n_rows,
+                                                 uint64_t g0, int w, uint64_t limit) {
+  constexpr int NW = T / 32;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  for (int r = wi; r < T; r += NW) {
+    const uint64_t row = row0 + r;
+    if (row >= n_rows) break;
+    const uint64_t base = row * gpitch + g0;
+    for (int c = lane; c < w; c += 32)
+      if (base + c < limit) st_out(out + base + c, tile[r * sp + c]);
+  }
+}
+
+}  // namespace prng

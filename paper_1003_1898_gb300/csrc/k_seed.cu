@@ -1,0 +1,105 @@
+// k_seed.cu -- on-device seeding of every stream of a handle (the paper
+// initialises its lag tables on the GPU too, Section 3.1).
+//
+// Stream i takes s = splitmix64(seed + i) and maps it into its generator's
+// seed range, then runs the generator's own table initialisation:
+//   GGL      x0 = 1 + s mod (2^31 - 2)
+//   XOR128   (x, y, z, w) = 32-bit halves of s and of splitmix64(s)
+//   RANECU   s1 = 1 + lo32(s) mod (m1 - 1), s2 = 1 + hi32(s) mod (m2 - 1)
+//   RANMAR   RMARIN(ij = lo32(s) mod 31329, kl = hi32(s) mod 30082)
+//   RANLUX   24 words from the MLCG 40014 mod 2147483563 started at
+//            s mod 2147483563 (19780503 when that is 0), carry = (x_{-1} == 0)
+//   MT19937  init_genrand(lo32(s))
+#include "common.cuh"
+
+namespace prng {
+
+// SplitMix64 (Steele, Lea, Flood 2014): gamma increment, then mix64.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// RMARIN (James 1988, cited by Section 3.5): 97 entries of 24 bits, most
+// significant bit first, from the lagged product generator mod 179 and the
+// LCG (53 l + 1) mod 169.  Written in canonical order V[k] = U[97 - k].
+__device__ void rmarin_to_state(uint32_t ij, uint32_t kl, uint32_t* st, uint64_t n, uint64_t row) {
+  uint32_t i = (ij / 177) % 177 + 2, j = ij % 177 + 2;
+  uint32_t k = (kl / 169) % 178 + 1, l = kl % 169;
+  for (int ii = 1; ii <= 97; ii++) {
+    uint32_t acc = 0;
+    for (int b = 23; b >= 0; b--) {
+      const uint32_t m = ((i * j) % 179 * k) % 179;
+      i = j;
+      j = k;
+      k = m;
+      l = (53 * l + 1) % 169;
+      acc |= ((l * m) % 64 >= 32 ? 1u : 0u) << b;
+    }
+    st[(uint64_t)(97 - ii) * n + row] = acc;
+  }
+  st[97 * n + row] = 362436u;  // C_0 = 362436 / 2^24
+}
+
+__global__ void k_seed(int gen, uint64_t seed, uint64_t n, uint32_t* st) {
+  const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const uint64_t s = splitmix64(seed + row);
+  const uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32);
+  switch (gen) {
+    case GGL:
+      st[row] = (uint32_t)(1 + s % 2147483646ull);
+      break;
+    case XOR128: {
+      const uint64_t t = splitmix64(s);
+      uint32_t z = (uint32_t)t, w = (uint32_t)(t >> 32);
+      if ((lo | hi | z | w) == 0) w = 1;
+      st[row] = lo;
+      st[n + row] = hi;
+      st[2 * n + row] = z;
+      st[3 * n + row] = w;
+      break;
+    }
+    case RANECU:
+      st[row] = 1 + lo % 2147483562u;
+      st[n + row] = 1 + hi % 2147483398u;
+      break;
+    case RANMAR:
+      rmarin_to_state(lo % 31329u, hi % 30082u, st, n, row);
+      break;
+    case RANLUX: {
+      uint32_t x = (uint32_t)(s % 2147483563ull);
+      if (x == 0) x = 19780503u;
+      uint32_t last = 0;
+      for (int k = 0; k < 24; k++) {
+        x = mlcg_step<40014u, 85u>(x);
+        last = x & 0xFFFFFFu;
+        st[(uint64_t)k * n + row] = last;
+      }
+      st[24 * n + row] = (last == 0) ? 1u : 0u;
+      break;
+    }
+    case MT19937: {
+      uint32_t* mt = st + row * 624;
+      uint32_t v = lo;
+      mt[0] = v;
+      for (uint32_t k = 1; k < 624; k++) {
+        v = 1812433253u * (v ^ (v >> 30)) + k;
+        mt[k] = v;
+      }
+      break;
+    }
+  }
+}
+
+cudaError_t launch_seed(int gen, int p, uint64_t seed, uint64_t n, uint32_t* state, cudaStream_t s) {
+  (void)p;
+  if (n == 0) return cudaSuccess;
+  const int T = (gen == RANMAR || gen == MT19937) ? 64 : 256;
+  k_seed<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(gen, seed, n, state);
+  return cudaGetLastError();
+}
+
+}  // namespace prng

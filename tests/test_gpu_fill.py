@@ -1,0 +1,297 @@
+"""GPU parity: every output of the CUDA library against the CPU oracle.
+
+Integer work, so the bar is bit-exact for u32 and for f32 (every float is
+an exact scaling of an integer of at most 24 bits).  All calls go through
+the C ABI via the thin Python binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1003_1898_gb300 as P  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_1898_gb300 import build
+    build.build()
+    P.lib()
+
+
+def lux_of(gen, p=24):
+    return p if gen == "ranlux" else 0
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def fill(h, n_streams, n_per, dtype="u32", offset=0):
+    """Fill into a fresh buffer (optionally at an element offset)."""
+    tdt = torch.float32 if dtype == "f32" else torch.int32
+    buf = torch.full((n_streams * n_per + offset + 4,), -7, dtype=tdt, device="cuda")
+    view = buf[offset:offset + n_streams * n_per]
+    if dtype == "f32":
+        P.prng_fill_f32(h, view.data_ptr(), n_per)
+    else:
+        P.prng_fill_u32(h, view.data_ptr(), n_per)
+    torch.cuda.synchronize()
+    tail = buf[offset + n_streams * n_per:]
+    head = buf[:offset]
+    assert torch.all(tail == -7), "write past the end of the output"
+    assert torch.all(head == -7), "write before the start of the output"
+    return view.reshape(n_streams, n_per) if n_per else view
+
+
+# ------------------------------------------------------------ small full compare
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_small_config_every_element(gen):
+    ns, nper = inputs.SMALL["n_streams"], inputs.SMALL["n_per"]
+    lux = lux_of(gen)
+    ref_u, ref_f = oracle.fill(gen, inputs.SEED_BASE, ns, nper, luxury=lux, want_f32=True)
+    h = P.prng_create(gen, inputs.SEED_BASE, ns, lux)
+    h2 = P.prng_create(gen, inputs.SEED_BASE, ns, lux)
+    try:
+        got_u = u32(fill(h, ns, nper))
+        got_f = fill(h2, ns, nper, "f32").cpu().numpy()
+    finally:
+        P.prng_destroy(h)
+        P.prng_destroy(h2)
+    np.testing.assert_array_equal(got_u, ref_u)
+    np.testing.assert_array_equal(got_f.view(np.uint32), ref_f.view(np.uint32))
+
+
+@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS)
+def test_ranlux_luxury_levels_small(p):
+    ns, nper = 96, 1000
+    ref = oracle.fill("ranlux", 99, ns, nper, luxury=p)
+    h = P.prng_create("ranlux", 99, ns, p)
+    try:
+        got = u32(fill(h, ns, nper))
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------ ragged shapes and continuation
+
+SHAPES = [(1, 1), (1, 33), (3, 5), (31, 97), (129, 31), (130, 98), (257, 623), (65, 625), (33, 1000)]
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+@pytest.mark.parametrize("ns,nper", SHAPES)
+def test_ragged_shapes(gen, ns, nper):
+    lux = lux_of(gen, 97)
+    ref = oracle.fill(gen, 7, ns, nper, luxury=lux, want_f32=True)
+    h = P.prng_create(gen, 7, ns, lux)
+    h2 = P.prng_create(gen, 7, ns, lux)
+    try:
+        got = u32(fill(h, ns, nper))
+        gotf = fill(h2, ns, nper, "f32").cpu().numpy()
+    finally:
+        P.prng_destroy(h)
+        P.prng_destroy(h2)
+    np.testing.assert_array_equal(got, ref[0])
+    np.testing.assert_array_equal(gotf.view(np.uint32), ref[1].view(np.uint32))
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_successive_fills_continue_each_stream(gen):
+    lux = lux_of(gen, 223)
+    ns = 70
+    pieces = [1, 7, 24, 23, 100, 97, 3, 624, 625, 1, 64, 500]
+    total = sum(pieces)
+    ref = oracle.fill(gen, 0xABC, ns, total, luxury=lux)
+    h = P.prng_create(gen, 0xABC, ns, lux)
+    try:
+        col = 0
+        for i, k in enumerate(pieces):
+            dtype = "f32" if i % 3 == 2 else "u32"
+            got = fill(h, ns, k, dtype)
+            if dtype == "f32":
+                want = oracle.to_f32(gen, ref[:, col:col + k])
+                np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), want.view(np.uint32))
+            else:
+                np.testing.assert_array_equal(u32(got), ref[:, col:col + k])
+            col += k
+    finally:
+        P.prng_destroy(h)
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_skip_equals_discarded_fill(gen):
+    lux = lux_of(gen, 389)
+    ns = 40
+    for k, nper in [(1, 10), (23, 50), (24, 24), (97, 130), (1000, 33), (12345, 64)]:
+        ref = oracle.fill(gen, 5, ns, nper, luxury=lux, skip=k)
+        h = P.prng_create(gen, 5, ns, lux)
+        try:
+            P.prng_skip(h, k)
+            got = u32(fill(h, ns, nper))
+        finally:
+            P.prng_destroy(h)
+        np.testing.assert_array_equal(got, ref, err_msg=f"skip {k}")
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_misaligned_output_scalar_path(gen):
+    # Output starting 1 element past a 16-byte boundary forces the scalar
+    # copy-out path; n_per not a multiple of 4 as well.
+    lux = lux_of(gen, 48)
+    ns, nper = 77, 130
+    ref = oracle.fill(gen, 3, ns, nper, luxury=lux)
+    h = P.prng_create(gen, 3, ns, lux)
+    try:
+        got = u32(fill(h, ns, nper, offset=1))
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_state_checkpoint_roundtrip(gen):
+    lux = lux_of(gen, 97)
+    ns = 50
+    h = P.prng_create(gen, 11, ns, lux)
+    try:
+        fill(h, ns, 37)                     # leave RANLUX / MT mid-block
+        blob = P.prng_get_state(h)
+        a = u32(fill(h, ns, 700))
+        P.prng_set_state(h, blob)
+        b = u32(fill(h, ns, 700))
+        np.testing.assert_array_equal(a, b)
+        ref = oracle.fill(gen, 11, ns, 700, luxury=lux, skip=37)
+        np.testing.assert_array_equal(a, ref)
+        bad = bytearray(blob)
+        bad[8] ^= 1                          # generator id in the header
+        with pytest.raises(P.PrngError):
+            P.prng_set_state(h, bytes(bad))
+    finally:
+        P.prng_destroy(h)
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_reseed_restarts_streams(gen):
+    lux = lux_of(gen, 24)
+    ns = 33
+    h = P.prng_create(gen, 1, ns, lux)
+    try:
+        fill(h, ns, 55)
+        P.prng_reseed(h, 2)
+        got = u32(fill(h, ns, 200))
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got, oracle.fill(gen, 2, ns, 200, luxury=lux))
+
+
+def test_zero_length_fill_is_noop():
+    h = P.prng_create("mt19937", 9, 8, 0)
+    try:
+        P.prng_fill_u32(h, 0, 0)
+        got = u32(fill(h, 8, 10))
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got, oracle.fill("mt19937", 9, 8, 10))
+
+
+# ------------------------------------------------------------ jump-ahead
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+@pytest.mark.parametrize("n,chunks", [(1, 1), (1000, 7), (100003, 37), (65536, 65536), (50000, 1)])
+def test_jump_fill_small_every_element(gen, n, chunks):
+    x0 = inputs.JUMP_X0[gen]
+    ref = oracle.serial_fill(gen, x0, n)
+    out = torch.full((n + 4,), -7, dtype=torch.int32, device="cuda")
+    P.prng_fill_jump_u32(gen, x0, n, chunks, out.data_ptr())
+    outf = torch.full((n,), -7.0, dtype=torch.float32, device="cuda")
+    P.prng_fill_jump_f32(gen, x0, n, chunks, outf.data_ptr())
+    torch.cuda.synchronize()
+    got = u32(out)
+    np.testing.assert_array_equal(got[:n], ref)
+    assert np.all(got[n:] == np.uint32(2**32 - 7))
+    np.testing.assert_array_equal(outf.cpu().numpy().view(np.uint32),
+                                  oracle.to_f32(gen, ref).view(np.uint32))
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+def test_jump_fill_other_start(gen):
+    x0 = 123456789 if gen == "ggl" else (987654 | (13579 << 32))
+    n = 77777
+    out = torch.empty((n,), dtype=torch.int32, device="cuda")
+    P.prng_fill_jump_u32(gen, x0, n, 100, out.data_ptr())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(u32(out), oracle.serial_fill(gen, x0, n))
+
+
+# ------------------------------------------------------------ full sizes (sampled)
+
+def _sampled_rows_check(gen, lux, ns, nper, n_rows_checked, dtype="u32"):
+    h = P.prng_create(gen, inputs.SEED_BASE, ns, lux)
+    try:
+        tdt = torch.float32 if dtype == "f32" else torch.int32
+        out = torch.empty((ns, nper), dtype=tdt, device="cuda")
+        if dtype == "f32":
+            P.prng_fill_f32(h, out, nper)
+        else:
+            P.prng_fill_u32(h, out, nper)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(ns, n_rows_checked)
+        got = out[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        for i, r in enumerate(rows):
+            ref = oracle.fill(gen, inputs.SEED_BASE, 1, nper, luxury=lux, stream0=int(r))[0]
+            if dtype == "f32":
+                np.testing.assert_array_equal(got[i].view(np.uint32),
+                                              oracle.to_f32(gen, ref).view(np.uint32))
+            else:
+                np.testing.assert_array_equal(got[i].view(np.uint32), ref, err_msg=f"row {r}")
+        # properties over every element: range of the integer / float outputs
+        if dtype == "f32":
+            assert float(out.min()) >= 0.0 and float(out.max()) < 1.0
+            scaled = out.double() * 2.0**24
+            assert bool(torch.all(scaled == torch.floor(scaled)))
+        del out
+    finally:
+        P.prng_destroy(h)
+
+
+@pytest.mark.parametrize("gen", ["ggl", "xor128", "ranecu", "ranmar", "ranlux"])
+@pytest.mark.parametrize("dtype", ["u32", "f32"])
+def test_roofline_config_sampled(gen, dtype):
+    cfg = inputs.ROOFLINE
+    _sampled_rows_check(gen, lux_of(gen, 24), cfg["n_streams"], cfg["n_per"], 24, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "f32"])
+def test_roofline_config_mt_sampled(dtype):
+    cfg = inputs.ROOFLINE_MT
+    _sampled_rows_check("mt19937", 0, cfg["n_streams"], cfg["n_per"], 8, dtype)
+
+
+@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS)
+def test_luxury_sweep_config_sampled(p):
+    cfg = inputs.LUX_SWEEP
+    _sampled_rows_check("ranlux", p, cfg["n_streams"], cfg["n_per"], 8, "f32")
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+def test_jump_full_size_sampled(gen):
+    n, chunks = inputs.JUMP["n"], inputs.JUMP["n_chunks"]
+    x0 = inputs.JUMP_X0[gen]
+    out = torch.empty((n,), dtype=torch.int32, device="cuda")
+    P.prng_fill_jump_u32(gen, x0, n, chunks, out.data_ptr())
+    torch.cuda.synchronize()
+    pos = inputs.jump_offsets(n, chunks)
+    got = out[torch.as_tensor(pos.astype(np.int64), device="cuda")].cpu().numpy().view(np.uint32)
+    ref = oracle.serial_sample(gen, x0, pos)
+    np.testing.assert_array_equal(got, ref)
+    if gen == "ggl":
+        assert int(got[np.searchsorted(pos, 9999)]) == 1043618065
+    del out
