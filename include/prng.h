@@ -114,6 +114,16 @@ int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunk
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        float *d_out, void *stream);
 
+/* Launch tile used by fills of generator `gen` (for RANLUX: of luxury p)
+ * on this process: threads per CTA, staged draws per thread per tile
+ * (RANMAR: 97, MT19937: 624) and staging buffers (1 or 2).  Set by the
+ * autotuner; only the combinations compiled into the library are accepted
+ * (PRNG_EUNSUPPORTED otherwise).  Not thread-safe against concurrent fills. */
+int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t cols,
+                  uint32_t stages);
+int prng_get_tile(prng_gen_t gen, uint32_t luxury, uint32_t *threads, uint32_t *cols,
+                  uint32_t *stages);
+
 /* Handle properties (any pointer may be NULL). */
 int prng_info(const prng_state *st, int32_t *gen, int32_t *p, uint32_t *n_streams,
               uint64_t *state_bytes);

@@ -51,6 +51,9 @@ def lib() -> ctypes.CDLL:
         "prng_fill_jump_f32": ([ctypes.c_int, u64, u64, u32, vp, vp], ctypes.c_int),
         "prng_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u32),
                        ctypes.POINTER(u64)], ctypes.c_int),
+        "prng_set_tile": ([ctypes.c_int, u32, u32, u32, u32], ctypes.c_int),
+        "prng_get_tile": ([ctypes.c_int, u32, ctypes.POINTER(u32), ctypes.POINTER(u32),
+                           ctypes.POINTER(u32)], ctypes.c_int),
         "prng_destroy": ([vp], None),
         "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -144,6 +147,17 @@ def prng_info(h) -> dict:
     _check(lib().prng_info(h, ctypes.byref(g), ctypes.byref(p), ctypes.byref(n), ctypes.byref(b)),
            "prng_info")
     return {"gen": g.value, "p": p.value, "n_streams": n.value, "state_bytes": b.value}
+
+
+def prng_set_tile(gen, luxury: int, threads: int, cols: int, stages: int):
+    _check(lib().prng_set_tile(_gen(gen), luxury, threads, cols, stages), "prng_set_tile")
+
+
+def prng_get_tile(gen, luxury: int = 0):
+    t, c, s = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().prng_get_tile(_gen(gen), luxury, ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)),
+           "prng_get_tile")
+    return (t.value, c.value, s.value)
 
 
 def prng_destroy(h):

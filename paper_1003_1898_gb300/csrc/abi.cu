@@ -77,7 +77,9 @@ int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t
     case RANMAR: e = launch_fill_ranmar(d, t, s); break;
     case RANLUX: e = launch_fill_ranlux(d, t, s); break;
     case MT19937: e = launch_fill_mt(d, t, s); break;
-    default: e = launch_fill_simple(st->gen, d, t, s); break;
+    default:  // GGL, XOR128, RANECU: lane-parallel tiles have 128 columns
+      e = t.cols == 128 ? launch_fill_mlcg(st->gen, d, t, s) : launch_fill_simple(st->gen, d, t, s);
+      break;
   }
   if (e != cudaSuccess) return PRNG_ECUDA;
   st->pos = advance_pos(st->gen, st->pos, n_per);
@@ -109,23 +111,54 @@ int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, 
   d.x0 = x0;
   d.f32 = f32;
   d.jump = 1;
-  if (launch_fill_simple(gen, d, default_tile(gen, 0), s) != cudaSuccess) return PRNG_ECUDA;
+  Tile t = default_tile(gen, 0);
+  if (t.cols != 128) t = Tile{256, 128, 1};  // jump chunks always run lane-parallel
+  if (launch_fill_mlcg(gen, d, t, s) != cudaSuccess) return PRNG_ECUDA;
   return PRNG_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Tiles compiled into the kernels, per generator family.
+bool tile_supported(int gen, Tile t) {
+  static const Tile simple[] = {{128, 32, 1}, {128, 32, 2}, {128, 64, 1}, {256, 32, 1}};
+  static const Tile mlcg[] = {{128, 128, 1}, {256, 128, 1}};
+  static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1}};
+  static const Tile mar[] = {{64, 97, 1}, {128, 97, 1}};
+  static const Tile mt[] = {{64, 624, 1}, {128, 624, 1}, {256, 624, 1}};
+  const Tile* list = simple;
+  int n = 4;
+  if ((gen == GGL || gen == RANECU) && t.cols == 128) { list = mlcg; n = 2; }
+  else if (gen == RANLUX) { list = lux; n = 3; }
+  else if (gen == RANMAR) { list = mar; n = 2; }
+  else if (gen == MT19937) { list = mt; n = 3; }
+  for (int i = 0; i < n; i++)
+    if (list[i].threads == t.threads && list[i].cols == t.cols && list[i].stages == t.stages)
+      return true;
+  return false;
+}
+
+int lux_index(int p) {
+  switch (p) { case 24: return 0; case 48: return 1; case 97: return 2; case 223: return 3; default: return 4; }
+}
+
+// Per generator (RANLUX: per p) launch tiles; slot 5 + i is RANLUX level i.
+Tile g_tiles[10] = {{128, 128, 1}, {128, 32, 1}, {128, 128, 1}, {128, 97, 1}, {128, 48, 1},
+                    {128, 624, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}};
+
+int tile_slot(int gen, int p) {
+  if (gen != RANLUX) return gen;
+  const int i = lux_index(p);
+  return i == 0 ? RANLUX : 5 + i;
 }
 
 }  // namespace
 
 namespace prng {
 
-Tile default_tile(int gen, int p) {
-  (void)p;
-  switch (gen) {
-    case RANMAR: return Tile{64, 97};
-    case RANLUX: return Tile{128, 48};
-    case MT19937: return Tile{128, 624};
-    default: return Tile{128, 32};
-  }
-}
+Tile default_tile(int gen, int p) { return g_tiles[tile_slot(gen, p)]; }
 
 }  // namespace prng
 
@@ -279,6 +312,37 @@ int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunk
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        float* d_out, void* stream) {
   return jump_impl((int)gen, x0, n, n_chunks, d_out, 1, static_cast<cudaStream_t>(stream));
+}
+
+int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t cols,
+                  uint32_t stages) {
+  const int g = (int)gen;
+  if (g < 0 || g > 5) return PRNG_EGEN;
+  int p = 0;
+  if (g == RANLUX) {
+    p = luxury_to_p(luxury);
+    if (p < 0) return PRNG_ELUXURY;
+  }
+  const Tile t{(int)threads, (int)cols, (int)stages};
+  if (!tile_supported(g, t)) return PRNG_EUNSUPPORTED;
+  g_tiles[tile_slot(g, p)] = t;
+  return PRNG_OK;
+}
+
+int prng_get_tile(prng_gen_t gen, uint32_t luxury, uint32_t* threads, uint32_t* cols,
+                  uint32_t* stages) {
+  const int g = (int)gen;
+  if (g < 0 || g > 5) return PRNG_EGEN;
+  int p = 0;
+  if (g == RANLUX) {
+    p = luxury_to_p(luxury);
+    if (p < 0) return PRNG_ELUXURY;
+  }
+  const Tile t = g_tiles[tile_slot(g, p)];
+  if (threads) *threads = (uint32_t)t.threads;
+  if (cols) *cols = (uint32_t)t.cols;
+  if (stages) *stages = (uint32_t)t.stages;
+  return PRNG_OK;
 }
 
 int prng_info(const prng_state* st, int32_t* gen, int32_t* p, uint32_t* n_streams,

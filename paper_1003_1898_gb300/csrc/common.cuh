@@ -48,9 +48,11 @@ struct FillDesc {
 struct Tile {
   int threads;   // threads per CTA (streams per CTA for thread-per-stream kernels)
   int cols;      // staged columns per tile
+  int stages;    // staging buffers (1 or 2)
 };
 
 cudaError_t launch_fill_simple(int gen, const FillDesc& d, Tile t, cudaStream_t s);
+cudaError_t launch_fill_mlcg(int gen, const FillDesc& d, Tile t, cudaStream_t s);
 cudaError_t launch_fill_ranmar(const FillDesc& d, Tile t, cudaStream_t s);
 cudaError_t launch_fill_ranlux(const FillDesc& d, Tile t, cudaStream_t s);
 cudaError_t launch_fill_mt(const FillDesc& d, Tile t, cudaStream_t s);
@@ -65,15 +67,19 @@ Tile default_tile(int gen, int p);
 
 __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
-// x <- A x mod (2^31 - C) for a multiplier A < 2^16 and a small C: the
-// 47-bit product is folded once with 2^31 = C (mod m), then one conditional
-// subtraction (unsigned min) brings it below m.  Same integer as the
-// paper's Schrage evaluation (Appendix A, eq. RANECU1), other route.
+// x <- A x mod (2^31 - C) for a multiplier A < 2^16 and a small C.  With
+// p = A x = hi 2^31 + lo31, 2^31 = C (mod m) gives A x = lo31 + C hi, which
+// is below 2^31 + 2^24, so one conditional subtraction (unsigned min) ends
+// the reduction.  hi = umulhi(x, 2A), and lo31 + C hi = (A x mod 2^32) -
+// hi m (mod 2^32), so the fold is three multiply-adds and only the final
+// subtraction and min use the integer ALU.  Same integer as the paper's
+// Schrage evaluation (Appendix A, eq. RANECU1), other route.
 template <uint32_t A, uint32_t C>
 __device__ __forceinline__ uint32_t mlcg_step(uint32_t x) {
   constexpr uint32_t M = 0x80000000u - C;
-  const uint64_t p = (uint64_t)x * A;
-  const uint32_t r = ((uint32_t)p & 0x7FFFFFFFu) + (uint32_t)(p >> 31) * C;
+  const uint32_t lo = x * A;
+  const uint32_t hi = __umulhi(x, 2u * A);
+  const uint32_t r = lo - hi * M;
   return umin32(r, r - M);
 }
 
@@ -130,5 +136,79 @@ __device__ __forceinline__ void copy_rows_scalar(const uint32_t* tile, int sp, u
       if (base + c < limit) st_out(out + base + c, tile[r * sp + c]);
   }
 }
+
+// Column-major staging tile of a thread-per-stream kernel: column c (the
+// c-th staged draw) of the CTA's row t sits at s[c * (T + 1) + t], so a
+// warp's 32 rows writing the same column hit 32 consecutive words (any
+// column, even one known only at run time), and the +1 skew keeps the
+// transposed reads below conflict-free.
+//
+// ColFlusher writes staged columns [0, w) to out at columns g0 .. g0 + w - 1
+// of rows row0 + t.  Lane (ro = lane & 3, qq = lane >> 2) handles row ro of
+// a 4-row group and 16-byte chunk qq of an 8-chunk group: four scalar
+// shared loads (banks 4 qq + ro + i, all distinct) and one 16-byte store,
+// so each warp store covers 4 rows x 128 contiguous bytes.  Chunks are
+// aligned to global multiples of 4 columns; a chunk cut by the edge of the
+// staged range, or a row base without 16-byte alignment, falls back to
+// scalar stores.  Row pointers and the per-lane row count are computed once
+// per kernel, so a flush is a short loop of loads and stores.
+template <int T>
+struct ColFlusher {
+  static constexpr int SP = T + 1, NW = T / 32, RIT = T / (4 * NW);  // row groups per warp
+  uint32_t* gp;       // this lane's first row, column 0
+  uint64_t rowstep;   // elements between this lane's consecutive rows
+  const uint32_t* sp; // shared tile at this lane's first row
+  int nrow;           // valid rows of this lane (<= RIT)
+  int qq;
+  bool vec_ok;
+
+  __device__ __forceinline__ void init(const uint32_t* s, uint32_t* out, uint64_t pitch,
+                                       uint64_t row0, uint64_t n_rows) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int r = wi * 4 + (lane & 3);
+    qq = lane >> 2;
+    rowstep = (uint64_t)NW * 4 * pitch;
+    gp = out + (row0 + r) * pitch;
+    sp = s + r;
+    const uint64_t left = n_rows > row0 + r ? n_rows - (row0 + r) : 0;   // rows from this one on
+    const uint64_t nr = (left + (NW * 4 - 1)) / (NW * 4);
+    nrow = nr < (uint64_t)RIT ? (int)nr : RIT;
+    vec_ok = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  }
+
+  __device__ __forceinline__ void flush(uint64_t g0, int w) const {
+    const uint64_t q0 = g0 >> 2;
+    const int nq = (int)(((g0 + (uint64_t)w + 3) >> 2) - q0);
+    for (int qb = 0; qb < nq; qb += 8) {
+      const int qi = qb + qq;
+      if (qi >= nq) continue;
+      const uint64_t gc = (q0 + qi) * 4;
+      const int c = (int)(gc - g0);
+      uint32_t* g = gp + gc;
+      if (vec_ok && c >= 0 && c + 4 <= w) {
+        const uint32_t* t = sp + c * SP;
+#pragma unroll
+        for (int k = 0; k < RIT; k++) {
+          if (k < nrow) {
+            uint4 v;
+            v.x = t[k * NW * 4];
+            v.y = t[k * NW * 4 + SP];
+            v.z = t[k * NW * 4 + 2 * SP];
+            v.w = t[k * NW * 4 + 3 * SP];
+            st_out4(g + k * rowstep, v);
+          }
+        }
+      } else {
+        for (int k = 0; k < nrow; k++) {
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            const int ci = c + i;
+            if (ci >= 0 && ci < w) st_out(g + k * rowstep + i, sp[ci * SP + k * NW * 4]);
+          }
+        }
+      }
+    }
+  }
+};
 
 }  // namespace prng

@@ -3,12 +3,12 @@
 //
 // One warp per stream, its 624-word table in shared memory.  The twist
 // X_{n+624} = X_{n+397} ^ (X_n^upper | X_{n+1}^lower) A is done in place in
-// 20 warp-wide chunks of 32 consecutive entries, in increasing order: entry
-// k reads old k and k+1 and either old k+397 (k < 227) or new k-227
-// (k >= 227, produced at least one chunk earlier), so a chunk needs only a
+// five warp-wide chunks of 128 consecutive entries, in increasing order:
+// entry k reads old k and k+1 and either old k+397 (k < 227) or new k-227
+// (k >= 227, produced in an earlier chunk), so a chunk needs only a
 // __syncwarp between its reads and its writes.  Each new word is tempered
-// and stored by the lane that produced it, so the 32 lanes write 32
-// consecutive outputs of the stream's row: coalesced without staging.
+// and stored by the lane that produced it: 32 lanes x 4 words are 512
+// consecutive bytes of the stream's row, written without staging.
 #include "common.cuh"
 
 namespace prng {
@@ -27,9 +27,72 @@ __device__ __forceinline__ uint32_t mt_conv(uint32_t t) {
   else return t;
 }
 
+__device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
+  const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
+  return f ^ (y >> 1) ^ ((0u - (y & 1u)) & 0x9908B0DFu);
+}
+
+// One twist of the warp's table (Appendix A, "Mersenne twister"), in place,
+// in five chunks of 128 entries; lane l owns entries k .. k+3, k = k0 + 4 l,
+// read and written with 16-byte shared accesses.  The lag X_{k+397} is old
+// for k < 227 and already replaced (X_{k-227}) from 227 on; both start one
+// word past a 16-byte boundary, so they come from two aligned 16-byte loads.
+// Only the lane holding k = 224..227 straddles the switch.  Each new word is
+// tempered and, if o != null, written to o[k] (16-byte stores when VEC);
+// PARTIAL: only entries k < take are written.
+template <bool F32, bool PARTIAL>
+__device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec) {
+#pragma unroll
+  for (int k0 = 0; k0 < 640; k0 += 128) {
+    const int k = k0 + 4 * lane;
+    const bool valid = k < 624;
+    uint4 a = make_uint4(0, 0, 0, 0), f = a;
+    uint32_t b = 0;
+    if (valid) {
+      a = *reinterpret_cast<const uint4*>(s + k);
+      b = s[k + 4 == 624 ? 0 : k + 4];
+      const bool old_lag = (k0 + 128 <= 227) || (k0 < 227 && k + 3 < 227);
+      const bool new_lag = (k0 >= 227) || k >= 227;
+      if (old_lag || new_lag) {
+        const int base = old_lag ? k + 396 : k - 228;
+        const uint4 q1 = *reinterpret_cast<const uint4*>(s + base);
+        const uint32_t q2 = s[base + 4];
+        f = make_uint4(q1.y, q1.z, q1.w, q2);
+      } else {  // k = 224: lags 621, 622, 623 (old) and 0 (new)
+        f = make_uint4(s[621], s[622], s[623], s[0]);
+      }
+    }
+    __syncwarp();
+    if (valid) {
+      uint4 v;
+      v.x = mt_mix(a.x, a.y, f.x);
+      v.y = mt_mix(a.y, a.z, f.y);
+      v.z = mt_mix(a.z, a.w, f.z);
+      v.w = mt_mix(a.w, b, f.w);
+      *reinterpret_cast<uint4*>(s + k) = v;
+      if (o != nullptr) {
+        uint4 t;
+        t.x = mt_conv<F32>(mt_temper(v.x));
+        t.y = mt_conv<F32>(mt_temper(v.y));
+        t.z = mt_conv<F32>(mt_temper(v.z));
+        t.w = mt_conv<F32>(mt_temper(v.w));
+        if (!PARTIAL && vec) {
+          st_out4(o + k, t);
+        } else {
+          if (!PARTIAL || k < take) st_out(o + k, t.x);
+          if (!PARTIAL || k + 1 < take) st_out(o + k + 1, t.y);
+          if (!PARTIAL || k + 2 < take) st_out(o + k + 2, t.z);
+          if (!PARTIAL || k + 3 < take) st_out(o + k + 3, t.w);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int WPB, bool F32>
 __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
-  __shared__ uint32_t table[WPB][624];
+  __shared__ __align__(16) uint32_t table[WPB][624];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const uint64_t row = (uint64_t)blockIdx.x * WPB + wi;
   if (row >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
@@ -50,28 +113,13 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
       for (uint64_t k = lane; k < h; k += 32) st_out(orow + k, mt_conv<F32>(mt_temper(s[mti + k])));
     j = h;
   }
-  while (j < n) {
-    const uint64_t take = (n - j) < 624 ? (n - j) : 624;
-#pragma unroll 4
-    for (int k0 = 0; k0 < 640; k0 += 32) {
-      const int k = k0 + lane;
-      uint32_t a = 0, b = 0, f = 0;
-      if (k < 624) {
-        a = s[k];
-        b = s[k == 623 ? 0 : k + 1];
-        f = s[k < 227 ? k + 397 : k - 227];
-      }
-      __syncwarp();
-      if (k < 624) {
-        const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
-        const uint32_t v = f ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
-        s[k] = v;
-        if (store && (uint64_t)k < take) st_out(orow + j + k, mt_conv<F32>(mt_temper(v)));
-      }
-      __syncwarp();
-    }
-    j += take;
+  // 16-byte output stores need the row position j to sit on a 16-byte boundary.
+  const bool vec = store && ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
+  while (n - j >= 624) {
+    mt_twist<F32, false>(s, lane, store ? orow + j : nullptr, 624, vec);
+    j += 624;
   }
+  if (j < n) mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)(n - j), false);
   for (int k = lane; k < 624; k += 32) gs[k] = s[k];
 }
 

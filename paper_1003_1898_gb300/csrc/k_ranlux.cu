@@ -1,32 +1,87 @@
 // k_ranlux.cu -- RANLUX fill and skip (Section 3.6; Appendix A, "AWC and SWB"
 // and "RANLUX").
 //
-// One thread per stream.  The 24-word RCARRY ring and the borrow live in
-// registers: the ring is walked 24 steps at a time with compile-time phase,
-// so every lag index (x_{n-10}, x_{n-24}) is a fixed register.  A luxury
-// cycle is 24 delivered steps plus p - 24 discarded ones; p - 24 = 24 q + r
-// runs as q unrolled 24-step groups, r single steps and one fixed register
-// permutation that re-aligns the ring.  Runtime-length pieces (the head of a
-// fill that resumes mid-block, the tail of a short fill) take guarded steps
-// followed by a barrel rotation (5 conditional fixed permutations).
+// One thread per stream.  In the hot loop the 24-word RCARRY ring and the
+// borrow live in registers and the ring is walked 24 steps at a time with a
+// compile-time phase, so both lags (x_{n-10}, x_{n-24}) are fixed registers
+// and no register is indexed at run time; eight steps at a time run as one
+// subtract-with-borrow chain (swb8).  A luxury cycle is 24 delivered
+// steps plus p - 24 discarded ones; p - 24 = 24 q + r runs as q unrolled
+// 24-step groups, r single steps and one fixed register permutation.
 //
-// Delivered values are staged per thread into a shared-memory row (odd row
-// pitch: conflict-free scalar stores) and written out row by row when the
-// tile is full, which makes the stream-major HBM writes contiguous.
+// The pieces whose length is only known at run time -- the head of a fill
+// that resumes inside a block and the tail of a fill that stops inside one --
+// run on a copy of the ring in shared memory with run-time indices (a few
+// dozen steps per call), and the registers are loaded from / stored to that
+// copy with the matching rotation.
+//
+// Delivered draws are staged in a column-major shared tile (see ColFlusher)
+// and written out 16 bytes at a time, so the stream-major HBM writes are
+// contiguous runs of each row.
 #include "common.cuh"
 
 namespace prng {
+
+// In registers each word is held as X = x * 2^8 (the 24-bit value in the
+// high bits, low byte 0).  Then one 32-bit subtract-with-borrow computes an
+// SWB step exactly: X10 - X24 - c has x10 - x24 - c (mod 2^24) in its high
+// 24 bits, and it borrows out of bit 31 exactly when x10 - x24 - c < 0,
+// because the low bytes of both operands are 0.  Only the low byte needs
+// clearing (it becomes 0xFF when c = 1).
 
 // One SWB step at compile-time ring phase k: V[j] = R[(j + k) % 24],
 // x_n = (x_{n-10} - x_{n-24} - c) mod 2^24, c = borrow.
 __device__ __forceinline__ void swb_step(uint32_t (&R)[24], uint32_t& c, const int k) {
   const int i0 = k % 24, i14 = (k + 14) % 24;
-  const int32_t t = (int32_t)R[i14] - (int32_t)R[i0] - (int32_t)c;
-  c = (uint32_t)t >> 31;
-  R[i0] = (uint32_t)t & 0xFFFFFFu;
+  const uint32_t a = R[i14];
+  const uint32_t t = a - R[i0] - c;
+  c = t > a ? 1u : 0u;          // borrow: R[i0] + c > a (no overflow, low bytes are 0)
+  R[i0] = t & 0xFFFFFF00u;
 }
 
-// Re-align after s steps: new R[j] = R[(j + s) % 24] (s a compile-time value).
+// Steps K0 .. K0+7 as one chain of subtract-with-borrow instructions; the
+// borrow travels in the carry flag, so the serial dependence per step is a
+// single instruction.  The lags (k + 14) % 24 of these steps never fall in
+// [K0, K0 + 8), so they are plain inputs.
+template <int K0>
+__device__ __forceinline__ void swb8(uint32_t (&R)[24], uint32_t& c) {
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "sub.cc.u32 t, 0, %8;\n\t"
+      "subc.cc.u32 %0, %9, %0;\n\t"
+      "and.b32 %0, %0, -256;\n\t"
+      "subc.cc.u32 %1, %10, %1;\n\t"
+      "and.b32 %1, %1, -256;\n\t"
+      "subc.cc.u32 %2, %11, %2;\n\t"
+      "and.b32 %2, %2, -256;\n\t"
+      "subc.cc.u32 %3, %12, %3;\n\t"
+      "and.b32 %3, %3, -256;\n\t"
+      "subc.cc.u32 %4, %13, %4;\n\t"
+      "and.b32 %4, %4, -256;\n\t"
+      "subc.cc.u32 %5, %14, %5;\n\t"
+      "and.b32 %5, %5, -256;\n\t"
+      "subc.cc.u32 %6, %15, %6;\n\t"
+      "and.b32 %6, %6, -256;\n\t"
+      "subc.cc.u32 %7, %16, %7;\n\t"
+      "and.b32 %7, %7, -256;\n\t"
+      "subc.u32 %8, 0, 0;\n\t"
+      "and.b32 %8, %8, 1;\n\t"
+      "}"
+      : "+r"(R[K0]), "+r"(R[K0 + 1]), "+r"(R[K0 + 2]), "+r"(R[K0 + 3]), "+r"(R[K0 + 4]),
+        "+r"(R[K0 + 5]), "+r"(R[K0 + 6]), "+r"(R[K0 + 7]), "+r"(c)
+      : "r"(R[(K0 + 14) % 24]), "r"(R[(K0 + 15) % 24]), "r"(R[(K0 + 16) % 24]),
+        "r"(R[(K0 + 17) % 24]), "r"(R[(K0 + 18) % 24]), "r"(R[(K0 + 19) % 24]),
+        "r"(R[(K0 + 20) % 24]), "r"(R[(K0 + 21) % 24]));
+}
+
+// 24 steps from phase 0 (the ring returns to phase 0).
+__device__ __forceinline__ void swb24(uint32_t (&R)[24], uint32_t& c) {
+  swb8<0>(R, c);
+  swb8<8>(R, c);
+  swb8<16>(R, c);
+}
+
+// new R[j] = R[(j + s) % 24] for a compile-time s.
 __device__ __forceinline__ void rotate_fixed(uint32_t (&R)[24], const int s) {
   uint32_t tmp[24];
 #pragma unroll
@@ -35,13 +90,12 @@ __device__ __forceinline__ void rotate_fixed(uint32_t (&R)[24], const int s) {
   for (int j = 0; j < 24; j++) R[j] = tmp[j];
 }
 
-// Re-align after a runtime number of steps h in [0, 24).
-__device__ __forceinline__ void rotate_runtime(uint32_t (&R)[24], int h) {
-  if (h & 1) rotate_fixed(R, 1);
-  if (h & 2) rotate_fixed(R, 2);
-  if (h & 4) rotate_fixed(R, 4);
-  if (h & 8) rotate_fixed(R, 8);
-  if (h & 16) rotate_fixed(R, 16);
+// Output of a word held as X = x * 2^8: x itself, or x * 2^-24 = X * 2^-32
+// (X has at most 24 significant bits, so the conversion is exact).
+template <bool F32>
+__device__ __forceinline__ uint32_t lux_out(uint32_t X) {
+  if constexpr (F32) return __float_as_uint(__uint2float_rn(X) * 0x1p-32f);
+  else return X >> 8;
 }
 
 template <bool F32>
@@ -50,105 +104,139 @@ __device__ __forceinline__ uint32_t lux_conv(uint32_t x) {
   else return x;
 }
 
-// p - 24 discarded steps; leaves the ring at phase 0.
+// p - 24 discarded steps from phase 0; leaves the ring at phase 0.
 template <int P>
 __device__ __forceinline__ void discard_cycle(uint32_t (&R)[24], uint32_t& c) {
   constexpr int D = P - 24, Q = D / 24, RR = D % 24;
-  for (int g = 0; g < Q; g++) {
-#pragma unroll
-    for (int k = 0; k < 24; k++) swb_step(R, c, k);
-  }
+#pragma unroll 1
+  for (int g = 0; g < Q; g++) swb24(R, c);
 #pragma unroll
   for (int k = 0; k < RR; k++) swb_step(R, c, k);
   if constexpr (RR != 0) rotate_fixed(R, RR);
 }
 
+// `cnt` SWB steps on a ring held in shared memory (ring[j * SP], phase
+// `ph`), emitting each new word to out_col[k * SP] when emit is set.
+template <int SP, bool F32>
+__device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int cnt,
+                                        uint32_t* out_col, bool emit) {
+  for (int k = 0; k < cnt; k++) {
+    const int i14 = ph + 14 < 24 ? ph + 14 : ph - 10;
+    const int32_t t = (int32_t)ring[i14 * SP] - (int32_t)ring[ph * SP] - (int32_t)c;
+    c = (uint32_t)t >> 31;
+    const uint32_t x = (uint32_t)t & 0xFFFFFFu;
+    ring[ph * SP] = x;
+    if (emit) out_col[k * SP] = lux_conv<F32>(x);
+    ph = ph + 1 < 24 ? ph + 1 : 0;
+  }
+  return ph;
+}
+
 template <int T, int KT, int P, bool F32>
-__global__ void __launch_bounds__(T) k_fill_ranlux(const FillDesc d) {
-  constexpr int SP = KT + 1;  // odd pitch: a warp's scalar stores hit 32 banks
-  extern __shared__ uint32_t smem[];
+__global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
+  static_assert(KT >= 48, "the tile must hold a partial block next to the 24-word scratch ring");
+  constexpr int SP = T + 1;
+  extern __shared__ uint32_t smem[];          // KT columns of SP words
   const int tid = threadIdx.x;
   const uint64_t row0 = (uint64_t)blockIdx.x * T;
   const uint64_t row = row0 + tid;
   const bool active = row < d.n_rows;
   const uint64_t nr = d.n_rows;
-
-  uint32_t R[24];
-  uint32_t c = 0;
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < 24; j++) R[j] = d.state[j * nr + row];
-    c = d.state[24 * nr + row];
-  } else {
-#pragma unroll
-    for (int j = 0; j < 24; j++) R[j] = 0;
-  }
-
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  uint32_t* my = smem + tid * SP;
-  int fill = 0;        // staged columns (uniform)
-  uint64_t g0 = 0;     // output column of staged column 0
+  ColFlusher<T> fl;
+  fl.init(smem, out, d.pitch, row0, nr);
+  uint32_t* col = smem + tid;                 // this thread's row of the tile (stride SP)
+  uint32_t* ring = smem + 24 * SP + tid;      // scratch ring in tile columns 24..47
+
+  const uint64_t n = d.n_per;
+  const int pos0 = (int)d.pos;
+  int fill = 0;
+  uint64_t g0 = 0, j = 0;
+  uint32_t R[24];
+  uint32_t c = 0;
 
   auto flush = [&]() {
     __syncthreads();
-    copy_rows_scalar<T>(smem, SP, out, d.pitch, row0, nr, g0, fill, d.limit);
+    if (store) fl.flush(g0, fill);
     __syncthreads();
     g0 += fill;
     fill = 0;
   };
 
-  // Deliver h (< 24, runtime) steps at phase 0, then re-align.
-  auto deliver_partial = [&](int h) {
-    if (store && fill + h > KT) flush();
+  if (pos0 < 24) {
+    // Finish the block a previous call left open: h draws on the shared copy.
+    const int h = (int)((uint64_t)(24 - pos0) < n ? (uint64_t)(24 - pos0) : n);
 #pragma unroll
-    for (int k = 0; k < 24; k++) {
-      if (k < h) {
-        swb_step(R, c, k);
-        if (store) my[fill + k] = lux_conv<F32>(R[k]);
+    for (int jj = 0; jj < 24; jj++) ring[jj * SP] = active ? d.state[jj * nr + row] : 0u;
+    c = active ? d.state[24 * nr + row] : 0u;
+    const int ph = swb_smem<SP, F32>(ring, 0, c, h, col, store);
+    fill = h;
+    j = h;
+    if (j == n) {  // the fill ends inside the open block
+      if (active) {
+        for (int jj = 0; jj < 24; jj++) {
+          const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
+          d.state[(uint64_t)jj * nr + row] = ring[src * SP];
+        }
+        d.state[24 * nr + row] = c;
       }
+      flush();
+      return;
     }
-    fill += h;
-    rotate_runtime(R, h);
-  };
-
-  const uint64_t n = d.n_per;
-  uint64_t j = 0;
-  int pos = (int)d.pos;
-  if (pos < 24 && n > 0) {  // finish the block a previous call left open
-    const int h = (int)((uint64_t)(24 - pos) < n ? (uint64_t)(24 - pos) : n);
-    deliver_partial(h);
-    j += h;
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) R[jj] = ring[((jj + h) % 24) * SP] << 8;  // h == 24 - pos0 here
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) R[jj] = active ? d.state[jj * nr + row] << 8 : 0u;
+    c = active ? d.state[24 * nr + row] : 0u;
   }
-  while (j < n) {  // the open block is complete here: discard, then deliver
+
+  // Whole blocks: discard p - 24, deliver 24, all in registers.
+  while (n - j >= 24) {
     discard_cycle<P>(R, c);
-    if (n - j >= 24) {
-      if (store && fill + 24 > KT) flush();
+    if (fill + 24 > KT) flush();
+    uint32_t* dst = col + fill * SP;
+    swb24(R, c);
+    if (store) {
 #pragma unroll
-      for (int k = 0; k < 24; k++) {
-        swb_step(R, c, k);
-        if (store) my[fill + k] = lux_conv<F32>(R[k]);
-      }
-      fill += 24;
-      j += 24;
-    } else {
-      const int h = (int)(n - j);
-      deliver_partial(h);
-      j += h;
+      for (int k = 0; k < 24; k++) dst[k * SP] = lux_out<F32>(R[k]);
     }
+    fill += 24;
+    j += 24;
   }
-  if (store && fill > 0) flush();
 
+  if (j < n) {
+    // Tail: the discard in registers, then m < 24 draws on the shared copy.
+    const int m = (int)(n - j);
+    discard_cycle<P>(R, c);
+    if (fill > 0) flush();
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) ring[jj * SP] = R[jj] >> 8;
+    const int ph = swb_smem<SP, F32>(ring, 0, c, m, col, store);
+    fill = m;
+    if (active) {
+      for (int jj = 0; jj < 24; jj++) {
+        const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
+        d.state[(uint64_t)jj * nr + row] = ring[src * SP];
+      }
+      d.state[24 * nr + row] = c;
+    }
+    flush();
+    return;
+  }
+
+  if (fill > 0) flush();
   if (active) {
 #pragma unroll
-    for (int jj = 0; jj < 24; jj++) d.state[jj * nr + row] = R[jj];
+    for (int jj = 0; jj < 24; jj++) d.state[jj * nr + row] = R[jj] >> 8;
     d.state[24 * nr + row] = c;
   }
 }
 
 template <int T, int KT, int P, bool F32>
 static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)T * (KT + 1) * sizeof(uint32_t);
+  constexpr size_t bytes = (size_t)KT * (T + 1) * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_fill_ranlux<T, KT, P, F32>,
@@ -157,7 +245,7 @@ static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
     configured = true;
   }
   const uint64_t grid = (d.n_rows + T - 1) / T;
-  k_fill_ranlux<T, KT, P, F32><<<(unsigned)grid, T, d.out ? bytes : 0, s>>>(d);
+  k_fill_ranlux<T, KT, P, F32><<<(unsigned)grid, T, bytes, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -181,6 +269,7 @@ static cudaError_t launch_lt(const FillDesc& d, cudaStream_t s) {
 cudaError_t launch_fill_ranlux(const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
   if (t.threads == 64) return launch_lt<64, 48>(d, s);
+  if (t.threads == 256) return launch_lt<256, 48>(d, s);
   return launch_lt<128, 48>(d, s);
 }
 

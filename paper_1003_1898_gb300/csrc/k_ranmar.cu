@@ -8,9 +8,10 @@
 // reads registers k and (k + 64) mod 97 and writes register k.  A fill of n
 // draws runs n / 97 full blocks and one guarded partial block; the final
 // phase is folded into the store-back addresses, so no register is ever
-// indexed at run time.  The Weyl term C_n = C_{n-1} - D mod M is a short
-// side chain.  Each block's 97 draws are staged in a shared-memory row and
-// written out row by row.
+// indexed at run time.  The Weyl term C_n = C_{n-1} - D mod M is evaluated
+// per draw as an offset of the block's entry value by a compile-time
+// constant, so no draw waits on the previous one.  Each block's 97 draws are staged in a column-major shared
+// tile and written out 16 bytes at a time (ColFlusher).
 #include "common.cuh"
 
 namespace prng {
@@ -18,15 +19,31 @@ namespace prng {
 constexpr uint32_t kRanmarD = 7654321u;    // Section 3.5: RM_CD * 2^24
 constexpr uint32_t kRanmarM = 16777213u;   // Section 3.5: RM_CM * 2^24
 
-// Draw at compile-time phase k: Y = V[0] - V[64] mod 2^24 replaces V[0];
-// C <- C - D (+M when negative); X = Y - C mod 2^24.
-__device__ __forceinline__ uint32_t ranmar_step(uint32_t (&R)[97], uint32_t& C, const int k) {
+// (k D) mod M, D = 7654321, M = 2^24 - 3 (a compile-time constant for the
+// unrolled steps).
+__host__ __device__ constexpr uint32_t ranmar_kd(int k) {
+  return (uint32_t)(((uint64_t)k * kRanmarD) % kRanmarM);
+}
+
+// Draw k (compile-time, 0-based) of a block whose Weyl term entered the
+// block as C0.  Y = V[0] - V[64] replaces V[0] (kept modulo 2^32; only its
+// low 24 bits matter).  The Weyl term after k+1 steps is C0 - (k+1) D mod M,
+// so each draw's C is an offset by a constant, independent of the previous
+// draw: with c = C0 - ((k+1) D mod M), C = c when c >= 0 and c + M otherwise,
+// and since M = 2^24 - 3, X = (Y - C) mod 2^24 = (Y - c + 3 [c < 0]) mod 2^24.
+__device__ __forceinline__ uint32_t ranmar_step(uint32_t (&R)[97], uint32_t C0, const int k) {
   const int i0 = k % 97, i64 = (k + 64) % 97;
-  const uint32_t y = (R[i0] - R[i64]) & 0xFFFFFFu;
+  const uint32_t y = R[i0] - R[i64];
   R[i0] = y;
-  C -= kRanmarD;
-  C += ((int32_t)C < 0) ? kRanmarM : 0u;
-  return (y - C) & 0xFFFFFFu;
+  const int32_t c = (int32_t)C0 - (int32_t)ranmar_kd(k + 1);
+  return (y - (uint32_t)c + 3u * ((uint32_t)c >> 31)) & 0xFFFFFFu;
+}
+
+// C0 after `steps` more draws.
+__device__ __forceinline__ uint32_t ranmar_advance_c(uint32_t C0, uint32_t steps) {
+  const uint32_t kd = (uint32_t)(((uint64_t)steps * kRanmarD) % kRanmarM);
+  const int32_t c = (int32_t)C0 - (int32_t)kd;
+  return c < 0 ? (uint32_t)(c + (int32_t)kRanmarM) : (uint32_t)c;
 }
 
 template <bool F32>
@@ -36,8 +53,8 @@ __device__ __forceinline__ uint32_t rm_conv(uint32_t x) {
 }
 
 template <int T, bool F32>
-__global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
-  constexpr int KT = 97, SP = 97;  // one block per tile; odd pitch
+__global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
+  constexpr int SP = T + 1;   // column-major tile of one 97-draw block (see ColFlusher)
   extern __shared__ uint32_t smem[];
   const int tid = threadIdx.x;
   const uint64_t row0 = (uint64_t)blockIdx.x * T;
@@ -58,7 +75,9 @@ __global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
 
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  uint32_t* my = smem + tid * SP;
+  ColFlusher<T> fl;
+  fl.init(smem, out, d.pitch, row0, nr);
+  uint32_t* col = smem + tid;
   const uint64_t n = d.n_per;
   const uint64_t nfull = n / 97;
   const int m = (int)(n % 97);
@@ -68,26 +87,28 @@ __global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
 #pragma unroll
     for (int k = 0; k < 97; k++) {
       const uint32_t x = ranmar_step(R, C, k);
-      if (store) my[k] = rm_conv<F32>(x);
+      if (store) col[k * SP] = rm_conv<F32>(x);
     }
+    C = ranmar_advance_c(C, 97);
     if (store) {
       __syncthreads();
-      copy_rows_scalar<T>(smem, SP, out, d.pitch, row0, nr, g0, KT, d.limit);
+      fl.flush(g0, 97);
       __syncthreads();
     }
-    g0 += KT;
+    g0 += 97;
   }
   if (m > 0) {
 #pragma unroll
     for (int k = 0; k < 97; k++) {
       if (k < m) {
         const uint32_t x = ranmar_step(R, C, k);
-        if (store) my[k] = rm_conv<F32>(x);
+        if (store) col[k * SP] = rm_conv<F32>(x);
       }
     }
+    C = ranmar_advance_c(C, (uint32_t)m);
     if (store) {
       __syncthreads();
-      copy_rows_scalar<T>(smem, SP, out, d.pitch, row0, nr, g0, m, d.limit);
+      fl.flush(g0, m);
     }
   }
 
@@ -96,7 +117,7 @@ __global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
 #pragma unroll
     for (int r = 0; r < 97; r++) {
       const int k = (r - m + 97) % 97;
-      d.state[(uint64_t)k * nr + row] = R[r];
+      d.state[(uint64_t)k * nr + row] = R[r] & 0xFFFFFFu;
     }
     d.state[97 * nr + row] = C;
   }
@@ -104,7 +125,7 @@ __global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
 
 template <int T, bool F32>
 static cudaError_t launch_m(const FillDesc& d, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)T * 97 * sizeof(uint32_t);
+  constexpr size_t bytes = (size_t)97 * (T + 1) * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_fill_ranmar<T, F32>,

@@ -1,14 +1,18 @@
-// k_simple.cu -- bulk fill for the register-state generators GGL (Section 3.2),
-// XOR128 (Section 3.3) and RANECU (Section 3.4), their jump-ahead
-// single-sequence fill, and the O(log k) skip of the two MLCG generators.
+// k_simple.cu -- staged bulk fill of the register-state generators XOR128
+// (Section 3.3), which has no cheap jump-ahead, and GGL (Section 3.2) and
+// RANECU (Section 3.4), whose fills can also run lane-parallel (k_mlcg.cu;
+// the launch tile selects which).
 //
 // One thread owns one stream (or one jump chunk) with its state in
 // registers.  Output is stream-major, so a warp's 32 streams write 32
 // different rows: each thread drafts K consecutive draws into its row of a
 // shared-memory tile with 16-byte stores, then the CTA writes the tile out
-// row by row (a warp covers 4 rows x 128 contiguous bytes per 16-byte store),
-// which turns the per-thread sequences into coalesced HBM writes.  The tile
-// is double-buffered so one barrier per tile suffices.
+// row by row (each 16-byte store instruction of a warp covers whole
+// 128-byte runs of rows),
+// which turns the per-thread sequences into coalesced HBM writes.  With S = 2
+// tiles one barrier per tile suffices; S = 1 halves the shared memory per
+// stream (two barriers per tile) so that every stream of a large handle can
+// be resident at once instead of running a partial second wave.
 #include "common.cuh"
 
 namespace prng {
@@ -18,15 +22,35 @@ struct GglGen {
   uint32_t x;
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) { x = st[row]; }
   __device__ __forceinline__ void store(uint32_t* st, uint64_t n, uint64_t row) const { st[row] = x; }
-  // Chunk start x0 a^e mod m (Appendix A, eq. MLCG in closed form).
-  __device__ __forceinline__ void jump_init(uint64_t x0, uint64_t e) {
-    x = mulmod_pm<1>(powmod_pm<1>(16807u, e), (uint32_t)x0);
-  }
   __device__ __forceinline__ void zero() { x = 1; }
   // x <- 16807 x mod (2^31 - 1)  (Section 3.2 constants).
   __device__ __forceinline__ uint32_t next() {
     x = mlcg_step<16807u, 1u>(x);
     return x;
+  }
+};
+
+struct RanecuGen {
+  static constexpr int SH = 7;
+  uint32_t s1, s2;
+  __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
+    s1 = st[row];
+    s2 = st[n + row];
+  }
+  __device__ __forceinline__ void store(uint32_t* st, uint64_t n, uint64_t row) const {
+    st[row] = s1;
+    st[n + row] = s2;
+  }
+  __device__ __forceinline__ void zero() { s1 = s2 = 1; }
+  // Section 3.4: m1 = 2147483563 = 2^31 - 85, m2 = 2147483399 = 2^31 - 249;
+  // combination z = s1 - s2, plus m1 - 1 when z < 1 (Appendix A, "Multiple
+  // recursive generators").
+  __device__ __forceinline__ uint32_t next() {
+    s1 = mlcg_step<40014u, 85u>(s1);
+    s2 = mlcg_step<40692u, 249u>(s2);
+    int32_t z = (int32_t)s1 - (int32_t)s2;
+    z += (z < 1) ? 2147483562 : 0;
+    return (uint32_t)z;
   }
 };
 
@@ -45,7 +69,6 @@ struct Xor128Gen {
     st[2 * n + row] = z;
     st[3 * n + row] = w;
   }
-  __device__ __forceinline__ void jump_init(uint64_t, uint64_t) {}
   __device__ __forceinline__ void zero() { x = y = z = 0; w = 1; }
   // Appendix A, "XORShift", scalar form of XOR128 with shifts 11, 19, 8.
   __device__ __forceinline__ uint32_t next() {
@@ -58,45 +81,26 @@ struct Xor128Gen {
   }
 };
 
-struct RanecuGen {
-  static constexpr int SH = 7;
-  uint32_t s1, s2;
-  __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
-    s1 = st[row];
-    s2 = st[n + row];
-  }
-  __device__ __forceinline__ void store(uint32_t* st, uint64_t n, uint64_t row) const {
-    st[row] = s1;
-    st[n + row] = s2;
-  }
-  // Each component jumped separately: s_j a_j^e mod m_j.
-  __device__ __forceinline__ void jump_init(uint64_t x0, uint64_t e) {
-    s1 = mulmod_pm<85u>(powmod_pm<85u>(40014u, e), (uint32_t)(x0 & 0xFFFFFFFFu));
-    s2 = mulmod_pm<249u>(powmod_pm<249u>(40692u, e), (uint32_t)(x0 >> 32));
-  }
-  __device__ __forceinline__ void zero() { s1 = s2 = 1; }
-  // Section 3.4: m1 = 2147483563 = 2^31 - 85, m2 = 2147483399 = 2^31 - 249;
-  // combination z = s1 - s2, plus m1 - 1 when z < 1 (Appendix A, "Multiple
-  // recursive generators").
-  __device__ __forceinline__ uint32_t next() {
-    s1 = mlcg_step<40014u, 85u>(s1);
-    s2 = mlcg_step<40692u, 249u>(s2);
-    int32_t z = (int32_t)s1 - (int32_t)s2;
-    z += (z < 1) ? 2147483562 : 0;
-    return (uint32_t)z;
-  }
-};
-
 template <class G, bool F32>
 __device__ __forceinline__ uint32_t conv(uint32_t v) {
   if constexpr (F32) return as_f32_bits<G::SH>(v);
   else return v;
 }
 
-template <class G, int T, int K, bool F32>
+// Row-major tile, thread t's K staged draws in row t.  16-byte chunk ch of
+// row t is stored at chunk slot ch ^ (t & 7): eight consecutive threads
+// writing the same chunk, or eight lanes reading eight chunks of one row,
+// touch eight different bank quads, without padding the rows.
+template <int K>
+__device__ __forceinline__ int swz(int row, int ch) { return ch ^ (row & 7); }
+
+template <class G, int T, int K, int S, bool F32>
 __global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
-  constexpr int SP = K + 4;  // row pitch in words: 16-byte stores of 8 rows hit 8 distinct bank quads
-  extern __shared__ __align__(16) uint32_t smem[];  // two tiles of T * SP words
+  static_assert(K % 32 == 0, "tile rows hold whole 8-chunk swizzle groups");
+  constexpr int CH = K / 4;          // 16-byte chunks per row
+  constexpr int RS = T / CH;         // rows one copy-out pass of the CTA covers
+  static_assert(RS % 8 == 0, "copy-out rows of one thread must share a swizzle phase");
+  extern __shared__ __align__(16) uint32_t smem[];  // S tiles of T * K words
   const int tid = threadIdx.x;
   const uint64_t row0 = (uint64_t)blockIdx.x * T;
   const uint64_t row = row0 + tid;
@@ -104,47 +108,64 @@ __global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
 
   G g;
   if (!active) g.zero();
-  else if (d.jump) g.jump_init(d.x0, row * d.pitch);
   else g.load(d.state, d.n_rows, row);
 
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool vec_ok = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  // Copy-out role of this thread: chunk `cch` of rows cr0 + RS k, k < CH.
+  const int cch = tid % CH, cr0 = tid / CH;
+  const int cslot = swz<K>(cr0, cch);           // (cr0 + RS k) & 7 == cr0 & 7
+  uint32_t* cg = out + (row0 + cr0) * d.pitch + 4 * cch;
+  const uint64_t cstep = (uint64_t)RS * d.pitch;
+  const uint64_t left = d.n_rows > row0 + cr0 ? d.n_rows - (row0 + cr0) : 0;
+  const int crows = left >= (uint64_t)RS * (CH - 1) + 1 ? CH : (int)((left + RS - 1) / RS);
   const uint64_t last_row = (row0 + T < d.n_rows ? row0 + T : d.n_rows) - 1;
+  const int sw = tid & 7;
+
   const uint64_t n = d.n_per;
   int buf = 0;
   for (uint64_t c0 = 0; c0 < n; c0 += K) {
     const int w = (n - c0 < (uint64_t)K) ? (int)(n - c0) : K;
-    uint32_t* const t = smem + buf * (T * SP);
-    uint32_t* my = t + tid * SP;
+    uint32_t* const t = smem + buf * (T * K);
+    uint32_t* my = t + tid * K;
     if (w == K) {
 #pragma unroll
-      for (int c = 0; c < K; c += 4) {
+      for (int c = 0; c < CH; c++) {
         uint4 v;
         v.x = conv<G, F32>(g.next());
         v.y = conv<G, F32>(g.next());
         v.z = conv<G, F32>(g.next());
         v.w = conv<G, F32>(g.next());
-        *reinterpret_cast<uint4*>(my + c) = v;
+        *reinterpret_cast<uint4*>(my + 4 * (c ^ sw)) = v;
       }
     } else {
-      for (int c = 0; c < w; c++) my[c] = conv<G, F32>(g.next());
+      for (int c = 0; c < w; c++) my[4 * ((c >> 2) ^ sw) + (c & 3)] = conv<G, F32>(g.next());
     }
     __syncthreads();
     if (w == K && vec_ok && last_row * d.pitch + c0 + K <= d.limit) {
-      constexpr int CH = K / 4;  // 16-byte chunks per row
-      for (int i = tid; i < T * CH; i += T) {
-        const int r = i / CH, ch = i % CH;
-        const uint64_t rr = row0 + r;
-        if (rr < d.n_rows)
-          st_out4(out + rr * d.pitch + c0 + 4 * ch,
-                  *reinterpret_cast<const uint4*>(t + r * SP + 4 * ch));
-      }
+      const uint32_t* src = t + cr0 * K + 4 * cslot;
+      uint32_t* dst = cg + c0;
+#pragma unroll
+      for (int k = 0; k < CH; k++)
+        if (k < crows)
+          st_out4(dst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
     } else {
-      copy_rows_scalar<T>(t, SP, out, d.pitch, row0, d.n_rows, c0, w, d.limit);
+      // Partial tile, unaligned output or a jump fill's last chunk: scalar
+      // stores, warp per row, lanes on consecutive columns.
+      constexpr int NW = T / 32;
+      const int lane = tid & 31, wi = tid >> 5;
+      for (int r = wi; r < T; r += NW) {
+        const uint64_t rr = row0 + r;
+        if (rr >= d.n_rows) break;
+        const uint64_t base = rr * d.pitch + c0;
+        for (int c = lane; c < w; c += 32)
+          if (base + c < d.limit) st_out(out + base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)]);
+      }
     }
-    buf ^= 1;
+    if constexpr (S == 1) __syncthreads();
+    else buf ^= 1;
   }
-  if (active && !d.jump) g.store(d.state, d.n_rows, row);
+  if (active) g.store(d.state, d.n_rows, row);
 }
 
 // Skip without output for XOR128 (plain stepping).
@@ -158,55 +179,41 @@ __global__ void k_skip_step(const FillDesc d) {
   g.store(d.state, d.n_rows, row);
 }
 
-// Skip of the MLCG generators in closed form: x <- a^k x mod m.
-__global__ void k_skip_mlcg(int gen, uint32_t* state, uint64_t n, uint64_t k) {
-  const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  if (gen == GGL) {
-    state[row] = mulmod_pm<1>(powmod_pm<1>(16807u, k), state[row]);
-  } else {
-    state[row] = mulmod_pm<85u>(powmod_pm<85u>(40014u, k), state[row]);
-    state[n + row] = mulmod_pm<249u>(powmod_pm<249u>(40692u, k), state[n + row]);
-  }
-}
-
-template <class G, int T, int K, bool F32>
+template <class G, int T, int K, int S, bool F32>
 static cudaError_t launch_tkf(const FillDesc& d, cudaStream_t s) {
-  constexpr size_t bytes = 2ull * T * (K + 4) * sizeof(uint32_t);
+  constexpr size_t bytes = (size_t)S * T * K * sizeof(uint32_t);
   static bool configured = false;  // attribute set once per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fill_simple<G, T, K, F32>,
+    cudaError_t e = cudaFuncSetAttribute(k_fill_simple<G, T, K, S, F32>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const uint64_t grid = (d.n_rows + T - 1) / T;
-  k_fill_simple<G, T, K, F32><<<(unsigned)grid, T, bytes, s>>>(d);
+  k_fill_simple<G, T, K, S, F32><<<(unsigned)grid, T, bytes, s>>>(d);
   return cudaGetLastError();
 }
 
-template <class G, int T, int K>
+template <class G, int T, int K, int S>
 static cudaError_t launch_tk(const FillDesc& d, cudaStream_t s) {
-  return d.f32 ? launch_tkf<G, T, K, true>(d, s) : launch_tkf<G, T, K, false>(d, s);
+  return d.f32 ? launch_tkf<G, T, K, S, true>(d, s) : launch_tkf<G, T, K, S, false>(d, s);
 }
 
+// Supported tiles: (threads, cols, stages).
 template <class G>
 static cudaError_t launch_g(const FillDesc& d, Tile t, cudaStream_t s) {
-  if (t.threads == 64 && t.cols == 32) return launch_tk<G, 64, 32>(d, s);
-  if (t.threads == 64 && t.cols == 64) return launch_tk<G, 64, 64>(d, s);
-  if (t.threads == 256 && t.cols == 32) return launch_tk<G, 256, 32>(d, s);
-  if (t.threads == 128 && t.cols == 64) return launch_tk<G, 128, 64>(d, s);
-  return launch_tk<G, 128, 32>(d, s);
+  if (t.threads == 128 && t.cols == 32 && t.stages == 2) return launch_tk<G, 128, 32, 2>(d, s);
+  if (t.threads == 128 && t.cols == 64 && t.stages == 1) return launch_tk<G, 128, 64, 1>(d, s);
+  if (t.threads == 256 && t.cols == 32 && t.stages == 1) return launch_tk<G, 256, 32, 1>(d, s);
+  return launch_tk<G, 128, 32, 1>(d, s);
 }
 
 cudaError_t launch_fill_simple(int gen, const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
-  if (d.out == nullptr) {  // skip
-    if (gen == XOR128) {
-      k_skip_step<Xor128Gen><<<(unsigned)((d.n_rows + 127) / 128), 128, 0, s>>>(d);
-      return cudaGetLastError();
-    }
-    return launch_skip_mlcg(gen, d.state, d.n_rows, d.n_per, s);
+  if (d.out == nullptr) {  // skip: plain stepping (the MLCG generators jump instead)
+    if (gen != XOR128) return cudaErrorInvalidValue;
+    k_skip_step<Xor128Gen><<<(unsigned)((d.n_rows + 127) / 128), 128, 0, s>>>(d);
+    return cudaGetLastError();
   }
   switch (gen) {
     case GGL: return launch_g<GglGen>(d, t, s);
@@ -214,12 +221,6 @@ cudaError_t launch_fill_simple(int gen, const FillDesc& d, Tile t, cudaStream_t 
     case RANECU: return launch_g<RanecuGen>(d, t, s);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_skip_mlcg(int gen, uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s) {
-  if (n == 0 || k == 0) return cudaSuccess;
-  k_skip_mlcg<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gen, state, n, k);
-  return cudaGetLastError();
 }
 
 }  // namespace prng

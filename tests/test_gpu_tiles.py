@@ -1,0 +1,70 @@
+"""Every launch tile compiled into the library gives the oracle's output
+(the autotuner may pick any of them)."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1003_1898_gb300 as P  # noqa: E402
+from paper_1003_1898_gb300 import tune  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_1898_gb300 import build
+    build.build()
+    P.lib()
+
+
+CASES = [(g, t) for g in P.GEN_NAMES for t in tune.tiles_for(g)]
+
+
+@pytest.mark.parametrize("gen,tile", CASES, ids=[f"{g}-{'x'.join(map(str, t))}" for g, t in CASES])
+def test_tile_parity(gen, tile):
+    lux = 223 if gen == "ranlux" else 0
+    saved = P.prng_get_tile(gen, lux)
+    P.prng_set_tile(gen, lux, *tile)
+    try:
+        ns = 300                                   # > 2 CTAs of 128, ragged last CTA
+        pieces = [700, 64, 33, 1300]               # continuation across fills, ragged tails
+        total = sum(pieces)
+        ref = oracle.fill(gen, 77, ns, total, luxury=lux)
+        h = P.prng_create(gen, 77, ns, lux)
+        try:
+            col = 0
+            for i, k in enumerate(pieces):
+                f32 = i % 2 == 1
+                out = torch.empty(ns * k, dtype=torch.float32 if f32 else torch.int32, device="cuda")
+                (P.prng_fill_f32 if f32 else P.prng_fill_u32)(h, out, k)
+                torch.cuda.synchronize()
+                got = out.cpu().numpy().reshape(ns, k).view(np.uint32)
+                want = ref[:, col:col + k]
+                if f32:
+                    want = oracle.to_f32(gen, want).view(np.uint32)
+                np.testing.assert_array_equal(got, want, err_msg=f"piece {i}")
+                col += k
+        finally:
+            P.prng_destroy(h)
+    finally:
+        P.prng_set_tile(gen, lux, *saved)
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+@pytest.mark.parametrize("tile", [t for t in tune.TILES["ggl"] if t[1] == 128])
+def test_tile_parity_jump(gen, tile):
+    saved = P.prng_get_tile(gen)
+    P.prng_set_tile(gen, 0, *tile)
+    try:
+        x0 = 1 if gen == "ggl" else (1 | (1 << 32))
+        n = 123457
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        P.prng_fill_jump_u32(gen, x0, n, 333, out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.serial_fill(gen, x0, n))
+    finally:
+        P.prng_set_tile(gen, 0, *saved)
