@@ -326,6 +326,15 @@ def run_ours(args, rank, world, local_rank):
     roof["write_only_gbs"] = write_only_gbs
     roof["frac_of_write_only"] = per[dl]["gbs"] / write_only_gbs
 
+    # Batched requests (20,000 mixed fills): one graph launch vs one plain
+    # re-seed + fill per request.
+    batched = None
+    if not args.no_batched:
+        del out_u, out_f
+        out_u = out_f = None
+        torch.cuda.empty_cache()
+        batched = measure_batched(P, dev, args)
+
     # end-to-end through the public API with host buffers: fill, then copy
     # every output to pinned host memory inside the timed region.
     e2e = None
@@ -334,7 +343,6 @@ def run_ours(args, rank, world, local_rank):
 
     for h in handles.values():
         P.prng_destroy(h)
-    del out_u, out_f
     if rank != 0:
         return
     cpu = None
@@ -353,6 +361,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"{world} independent partitions of the streams"},
         "clocks": clk.summary(),
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -361,6 +370,90 @@ def run_ours(args, rank, world, local_rank):
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_batched(P, dev, args):
+    """Config of 20,000 requests: lengths log-uniform in [1e2, 1e7], generator
+    uniform over the six (RANLUX p = 223), u32/f32 at random.  Both forms
+    re-seed every request's streams and fill them; the outputs are the same
+    bytes.  Latency of a request = its completion time after the first
+    launch of the pass (per-request events for the plain form; every request
+    of a batch completes with the batch)."""
+    import torch
+    from paper_1003_1898_gb300 import workloads as W
+    reqs = W.batched_requests(args.batch_requests)
+    sizes = [((q["n_streams"] * q["n_per"] + 3) // 4) * 4 for q in reqs]
+    offs = [0]
+    for z in sizes:
+        offs.append(offs[-1] + z)
+    buf = torch.empty(offs[-1], dtype=torch.int32, device=dev)
+    base = buf.data_ptr()
+    handles = [P.prng_create(q["gen"], q["seed"], q["n_streams"], q["luxury"]) for q in reqs]
+    fr = [{"st": h, "d_out": base + 4 * o, "n_per_stream": q["n_per"], "n_valid": q["n"],
+           "f32": q["f32"], "reseed": True, "seed": q["seed"]}
+          for h, q, o in zip(handles, reqs, offs)]
+    b = P.prng_batch_create(fr)
+    info = P.prng_batch_info(b)
+    numbers = info["numbers"]
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # batched: one graph launch per pass
+    for _ in range(2):
+        P.prng_batch_launch(b, sid)
+    torch.cuda.synchronize()
+    bt = []
+    for _ in range(args.batch_passes):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        P.prng_batch_launch(b, sid)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bt.append(e0.elapsed_time(e1))
+    # plain: re-seed and fill each request with its own launches
+    def plain(record):
+        done = []
+        e0 = ev()
+        e0.record(stream)
+        for h, q, o in zip(handles, reqs, offs):
+            P.prng_reseed(h, q["seed"], sid)
+            (P.prng_fill_f32 if q["f32"] else P.prng_fill_u32)(h, base + 4 * o, q["n_per"], sid)
+            if record:
+                e = ev()
+                e.record(stream)
+                done.append(e)
+        e1 = ev()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0, e1, done
+    plain(False)
+    pt, lat = [], []
+    for i in range(args.batch_passes):
+        t_host = time.perf_counter()
+        e0, e1, done = plain(i == 0)
+        pt.append(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host)))
+        if done:
+            lat = sorted(e0.elapsed_time(e) for e in done)
+    P.prng_batch_destroy(b)
+    for h in handles:
+        P.prng_destroy(h)
+    del buf
+    torch.cuda.empty_cache()
+    bms, pms = statistics.median(bt), statistics.median(pt)
+    pct = lambda xs, q: xs[min(len(xs) - 1, int(q * len(xs)))]
+    return {"requests": len(reqs), "numbers_per_pass": numbers, "work_items": info["items"],
+            "batched": {"ms_per_pass": bms, "numbers_per_s": numbers / (bms / 1e3),
+                        "p50_ms": bms, "p99_ms": bms, "launches_per_pass": 1},
+            "per_request": {"ms_per_pass": pms, "numbers_per_s": numbers / (pms / 1e3),
+                            "p50_ms": pct(lat, 0.50) if lat else None,
+                            "p99_ms": pct(lat, 0.99) if lat else None,
+                            "launches_per_pass": 2 * len(reqs)},
+            "speedup": pms / bms,
+            "note": "per-request time is the larger of the device span and the host "
+                    "enqueue time of its launches"}
 
 
 def measure_e2e(P, handles, seed_r, items, dev, args):
@@ -420,6 +513,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2**26)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-requests", type=int, default=20000)
+    ap.add_argument("--batch-passes", type=int, default=3)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -114,6 +114,48 @@ int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunk
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        float *d_out, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many fills on distinct handles run as one pass: the plan cuts every
+ * request into work items (a range of its streams), orders each generator
+ * family's items longest first and keeps them on the device; a launch runs
+ * the optional re-seeding of the flagged handles and then one persistent
+ * kernel per generator family that pops items from a device counter, as one
+ * CUDA graph launch.  The draws are exactly those of prng_reseed followed by
+ * prng_fill_u32/f32 on each handle alone (the paper's generators, Sections
+ * 3.2-3.7, unchanged). */
+typedef struct prng_fill_req {
+  prng_state *st;         /* handle to fill; each handle at most once per batch */
+  void *d_out;            /* device output, stream-major, pitch n_per_stream   */
+  uint64_t n_per_stream;  /* draws per stream (the handle advances by this)   */
+  uint64_t n_valid;       /* elements written: the first n_valid of the block
+                             (0 = all n_streams * n_per_stream)               */
+  uint64_t seed;          /* base seed used when reseed is set                */
+  uint32_t f32;           /* 0: uint32 output, 1: float output                */
+  uint32_t reseed;        /* 1: re-seed the handle from `seed` first          */
+} prng_fill_req;
+
+typedef struct prng_batch prng_batch;
+
+/* Plan a batch.  Copies the request list (handles must stay alive and must
+ * not be destroyed before the batch); allocates the work items, two
+ * descriptor buffers and the work counters.  PRNG_EBLOB if a handle appears
+ * twice. */
+int prng_batch_create(prng_batch **out, const prng_fill_req *reqs, uint32_t n_reqs);
+
+/* Run the batch once on `stream` (asynchronous).  Every handle's position
+ * advances as after its own fill.  The first launch on each of the two
+ * descriptor buffers captures the CUDA graph that later launches replay;
+ * launch k+2 waits on the host for launch k to finish with its buffer.
+ * Launches of one batch must be issued to one stream. */
+int prng_batch_launch(prng_batch *b, void *stream);
+
+/* Requests, work items and numbers written per launch. */
+int prng_batch_info(const prng_batch *b, uint32_t *n_requests, uint64_t *n_items,
+                    uint64_t *n_numbers);
+
+/* Wait for the batch's launches and free it (NULL accepted). */
+void prng_batch_destroy(prng_batch *b);
+
 /* Launch tile used by fills of generator `gen` (for RANLUX: of luxury p)
  * on this process: threads per CTA, staged draws per thread per tile
  * (RANMAR: 97, MT19937: 624) and staging buffers (1 or 2).  Set by the

@@ -23,6 +23,13 @@ STATE_WORDS = (1, 4, 2, 98, 25, 624)
 _lib = None
 
 
+class PrngFillReq(ctypes.Structure):
+    """struct prng_fill_req (include/prng.h)."""
+    _fields_ = [("st", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("n_per_stream", ctypes.c_uint64), ("n_valid", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("f32", ctypes.c_uint32), ("reseed", ctypes.c_uint32)]
+
+
 class PrngError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {prng_strerror(code)} (code {code})")
@@ -54,6 +61,11 @@ def lib() -> ctypes.CDLL:
         "prng_set_tile": ([ctypes.c_int, u32, u32, u32, u32], ctypes.c_int),
         "prng_get_tile": ([ctypes.c_int, u32, ctypes.POINTER(u32), ctypes.POINTER(u32),
                            ctypes.POINTER(u32)], ctypes.c_int),
+        "prng_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(PrngFillReq), u32], ctypes.c_int),
+        "prng_batch_launch": ([vp, vp], ctypes.c_int),
+        "prng_batch_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)],
+                            ctypes.c_int),
+        "prng_batch_destroy": ([vp], None),
         "prng_destroy": ([vp], None),
         "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -158,6 +170,40 @@ def prng_get_tile(gen, luxury: int = 0):
     _check(lib().prng_get_tile(_gen(gen), luxury, ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)),
            "prng_get_tile")
     return (t.value, c.value, s.value)
+
+
+def prng_batch_create(reqs) -> ctypes.c_void_p:
+    """reqs: iterable of dicts with keys st, d_out, n_per_stream and optional
+    n_valid, seed, f32, reseed."""
+    reqs = list(reqs)
+    arr = (PrngFillReq * len(reqs))()
+    for i, r in enumerate(reqs):
+        st = r["st"]
+        arr[i].st = st.value if isinstance(st, ctypes.c_void_p) else st
+        arr[i].d_out = _ptr(r["d_out"])
+        arr[i].n_per_stream = r["n_per_stream"]
+        arr[i].n_valid = r.get("n_valid", 0)
+        arr[i].seed = r.get("seed", 0) & (2**64 - 1)
+        arr[i].f32 = 1 if r.get("f32", False) else 0
+        arr[i].reseed = 1 if r.get("reseed", False) else 0
+    b = ctypes.c_void_p()
+    _check(lib().prng_batch_create(ctypes.byref(b), arr, len(reqs)), "prng_batch_create")
+    return b
+
+
+def prng_batch_launch(b, stream=None):
+    _check(lib().prng_batch_launch(b, _stream(stream)), "prng_batch_launch")
+
+
+def prng_batch_info(b) -> dict:
+    n, it, num = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().prng_batch_info(b, ctypes.byref(n), ctypes.byref(it), ctypes.byref(num)),
+           "prng_batch_info")
+    return {"requests": n.value, "items": it.value, "numbers": num.value}
+
+
+def prng_batch_destroy(b):
+    lib().prng_batch_destroy(b)
 
 
 def prng_destroy(h):

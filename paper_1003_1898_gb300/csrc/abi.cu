@@ -11,48 +11,14 @@
 
 #include "../../include/prng.h"
 #include "common.cuh"
+#include "handle.cuh"
 
 using namespace prng;
-
-struct prng_state {
-  int gen;
-  int p;                 // RANLUX luxury p (0 for the others)
-  uint64_t n_streams;
-  uint32_t* d_state;     // device state, layout in common.cuh
-  uint32_t pos;          // RANLUX: draws delivered from the open block; MT: mti
-  int device;
-};
 
 namespace {
 
 constexpr uint32_t kBlobMagic = 0x50524E47u;  // "PRNG"
 constexpr uint32_t kBlobVersion = 1u;
-
-int luxury_to_p(uint32_t luxury) {
-  static const int P[5] = {24, 48, 97, 223, 389};
-  if (luxury <= 4) return P[luxury];
-  for (int i = 0; i < 5; i++)
-    if ((int)luxury == P[i]) return P[i];
-  return -1;
-}
-
-uint32_t initial_pos(int gen) { return gen == MT19937 ? 624u : 0u; }
-
-// Position after n more draws (all streams move together).
-uint32_t advance_pos(int gen, uint32_t pos, uint64_t n) {
-  if (n == 0) return pos;
-  if (gen == RANLUX) {
-    const uint64_t h = pos < 24 ? (24 - pos < n ? 24 - pos : n) : 0;
-    const uint64_t r = n - h;
-    return r == 0 ? (uint32_t)(pos + h) : (uint32_t)((r - 1) % 24 + 1);
-  }
-  if (gen == MT19937) {
-    const uint64_t h = pos < 624 ? (624 - pos < n ? 624 - pos : n) : 0;
-    const uint64_t r = n - h;
-    return r == 0 ? (uint32_t)(pos + h) : (uint32_t)((r - 1) % 624 + 1);
-  }
-  return 0;
-}
 
 int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t s) {
   if (st == nullptr) return PRNG_ENULL;

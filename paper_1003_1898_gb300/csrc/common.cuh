@@ -152,27 +152,44 @@ __device__ __forceinline__ void copy_rows_scalar(const uint32_t* tile, int sp, u
 // staged range, or a row base without 16-byte alignment, falls back to
 // scalar stores.  Row pointers and the per-lane row count are computed once
 // per kernel, so a flush is a short loop of loads and stores.
-template <int T>
+// LIMITED: honour FillDesc::limit (batched requests whose last stream is
+// only partly wanted); single fills use the cheaper unlimited form.
+template <int T, bool LIMITED = false>
 struct ColFlusher {
   static constexpr int SP = T + 1, NW = T / 32, RIT = T / (4 * NW);  // row groups per warp
   uint32_t* gp;       // this lane's first row, column 0
   uint64_t rowstep;   // elements between this lane's consecutive rows
   const uint32_t* sp; // shared tile at this lane's first row
-  int nrow;           // valid rows of this lane (<= RIT)
+  int nrow;           // rows of this lane with at least one element to write (<= RIT)
+  int kcut;           // index (< nrow) of the row cut by the element limit, or RIT
+  uint64_t ccut;      // columns of that row still below the limit
   int qq;
   bool vec_ok;
 
+  // Rows row0 + r of `out` (pitch elements apart), writing only elements
+  // whose linear index is below `limit`.
   __device__ __forceinline__ void init(const uint32_t* s, uint32_t* out, uint64_t pitch,
-                                       uint64_t row0, uint64_t n_rows) {
+                                       uint64_t row0, uint64_t n_rows, uint64_t limit) {
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int r = wi * 4 + (lane & 3);
     qq = lane >> 2;
     rowstep = (uint64_t)NW * 4 * pitch;
     gp = out + (row0 + r) * pitch;
     sp = s + r;
-    const uint64_t left = n_rows > row0 + r ? n_rows - (row0 + r) : 0;   // rows from this one on
+    uint64_t rows = n_rows;                       // rows holding an element below the limit
+    if (LIMITED && pitch > 0 && (limit + pitch - 1) / pitch < rows) rows = (limit + pitch - 1) / pitch;
+    const uint64_t left = rows > row0 + r ? rows - (row0 + r) : 0;
     const uint64_t nr = (left + (NW * 4 - 1)) / (NW * 4);
     nrow = nr < (uint64_t)RIT ? (int)nr : RIT;
+    kcut = RIT;
+    ccut = 0;
+    if (LIMITED && pitch > 0 && limit < rows * pitch) {  // the last of those rows is partial
+      const uint64_t last = rows - 1;
+      if (last >= row0 + r && (last - (row0 + r)) % (NW * 4) == 0) {
+        kcut = (int)((last - (row0 + r)) / (NW * 4));
+        ccut = limit - last * pitch;
+      }
+    }
     vec_ok = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
   }
 
@@ -195,7 +212,13 @@ struct ColFlusher {
             v.y = t[k * NW * 4 + SP];
             v.z = t[k * NW * 4 + 2 * SP];
             v.w = t[k * NW * 4 + 3 * SP];
-            st_out4(g + k * rowstep, v);
+            if (!LIMITED || k != kcut || gc + 4 <= ccut) {
+              st_out4(g + k * rowstep, v);
+            } else {
+              if (gc < ccut) st_out(g + k * rowstep, v.x);
+              if (gc + 1 < ccut) st_out(g + k * rowstep + 1, v.y);
+              if (gc + 2 < ccut) st_out(g + k * rowstep + 2, v.z);
+            }
           }
         }
       } else {
@@ -203,7 +226,8 @@ struct ColFlusher {
 #pragma unroll
           for (int i = 0; i < 4; i++) {
             const int ci = c + i;
-            if (ci >= 0 && ci < w) st_out(g + k * rowstep + i, sp[ci * SP + k * NW * 4]);
+            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
+              st_out(g + k * rowstep + i, sp[ci * SP + k * NW * 4]);
           }
         }
       }

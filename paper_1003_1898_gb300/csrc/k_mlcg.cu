@@ -12,7 +12,7 @@
 // Rows are taken in a grid-stride loop.  Since every stream of a call
 // advances by the same n, the state left after the call is the stored state
 // times a^n, one multiplication per row with a^n computed once per warp.
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -55,82 +55,139 @@ __device__ __forceinline__ uint32_t lj_conv(uint32_t v) {
   else return v;
 }
 
+// Per-warp constants of one call: multipliers to a lane's first draw, to
+// the next 128-draw block and over the whole call (n draws).
+template <class G>
+struct LjConst {
+  uint32_t lane_mul[G::NC], block_mul[G::NC], fin_mul[G::NC];
+  __device__ __forceinline__ void init(int lane, uint64_t n) {
+#pragma unroll
+    for (int c = 0; c < G::NC; c++) {
+      lane_mul[c] = G::pow(c, 4 * lane + 1);
+      block_mul[c] = G::pow(c, 128);
+      fin_mul[c] = G::pow(c, n);
+    }
+  }
+};
+
+// One row (stream, or jump chunk whose start components are `base`) by one
+// warp: draws 0 .. nv-1 written to orow (row start), 16-byte stores when vec.
+template <class G, bool F32>
+__device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&base)[G::NC], int lane,
+                                       uint32_t* orow, uint64_t nv, bool vec) {
+  constexpr int NC = G::NC;
+  uint32_t s[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) s[c] = G::mul(c, K.lane_mul[c], base[c]);
+  orow += 4 * lane;
+  for (uint64_t c0 = 0; c0 < nv; c0 += 128) {
+    uint32_t t[NC], o[4];
+#pragma unroll
+    for (int c = 0; c < NC; c++) t[c] = s[c];
+    o[0] = lj_conv<G, F32>(G::out(t));
+#pragma unroll
+    for (int i = 1; i < 4; i++) {
+#pragma unroll
+      for (int c = 0; c < NC; c++) t[c] = G::step(c, t[c]);
+      o[i] = lj_conv<G, F32>(G::out(t));
+    }
+    if (vec && c0 + 128 <= nv) {
+      st_out4(orow + c0, make_uint4(o[0], o[1], o[2], o[3]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (c0 + 4 * lane + i < nv) st_out(orow + c0 + i, o[i]);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++) s[c] = G::mul(c, s[c], K.block_mul[c]);
+  }
+}
+
+// Stream `row` of a handle fill: load its state, write its row, store the
+// state advanced by n draws (lane 0).
+template <class G, bool F32>
+__device__ __forceinline__ void lj_stream(const LjConst<G>& K, const FillDesc& d, uint64_t row, int lane) {
+  constexpr int NC = G::NC;
+  uint32_t base[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) base[c] = d.state[c * d.n_rows + row];
+  uint64_t nv = d.n_per;
+  if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
+  uint32_t* out = static_cast<uint32_t*>(d.out);
+  const bool vec = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  lj_row<G, F32>(K, base, lane, out + row * d.pitch, nv, vec);
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; c++) d.state[c * d.n_rows + row] = G::mul(c, base[c], K.fin_mul[c]);
+  }
+}
+
 template <class G, int WPB, bool F32>
 __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
   constexpr int NC = G::NC;
   const int lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * WPB;
   const uint64_t wrow = (uint64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
-  const uint64_t n = d.n_per;
-  uint32_t* out = static_cast<uint32_t*>(d.out);
-  const bool vec_ok = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-
-  uint32_t lane_mul[NC], block_mul[NC], fin_mul[NC], jrow[NC], jstep[NC];
+  LjConst<G> K;
+  K.init(lane, d.n_per);
+  if (!d.jump) {
+    for (uint64_t row = wrow; row < d.n_rows; row += nwarps) lj_stream<G, F32>(K, d, row, lane);
+    return;
+  }
+  // Jump fill: chunk r starts at a^(r L) x0; this warp's chunks are nwarps apart.
+  uint32_t jrow[NC], jstep[NC];
 #pragma unroll
   for (int c = 0; c < NC; c++) {
-    lane_mul[c] = G::pow(c, 4 * lane + 1);
-    block_mul[c] = G::pow(c, 128);
-    fin_mul[c] = G::pow(c, n);
-    if (d.jump) {  // chunk r starts at a^(r L) x0; this warp's rows are nwarps apart
-      jrow[c] = G::mul(c, G::pow(c, wrow * d.pitch), G::x0_part(c, d.x0));
-      jstep[c] = G::pow(c, nwarps * d.pitch);
-    } else {
-      jrow[c] = jstep[c] = 0;
-    }
+    jrow[c] = G::mul(c, G::pow(c, wrow * d.pitch), G::x0_part(c, d.x0));
+    jstep[c] = G::pow(c, nwarps * d.pitch);
   }
-
+  uint32_t* out = static_cast<uint32_t*>(d.out);
+  const bool vec_ok = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
   for (uint64_t row = wrow; row < d.n_rows; row += nwarps) {
-    uint32_t base[NC], s[NC];
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      base[c] = d.jump ? jrow[c] : d.state[c * d.n_rows + row];
-      s[c] = G::mul(c, lane_mul[c], base[c]);
-    }
-    uint64_t nv = n;  // draws of this row to write (a jump fill's last chunk is shorter)
+    uint64_t nv = d.n_per;
     if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
-    uint32_t* orow = out + row * d.pitch + 4 * lane;
-    const bool vec = vec_ok && ((row * d.pitch) & 3) == 0;
-    for (uint64_t c0 = 0; c0 < nv; c0 += 128) {
-      uint32_t t[NC], o[4];
+    lj_row<G, F32>(K, jrow, lane, out + row * d.pitch, nv, vec_ok && ((row * d.pitch) & 3) == 0);
 #pragma unroll
-      for (int c = 0; c < NC; c++) t[c] = s[c];
-      o[0] = lj_conv<G, F32>(G::out(t));
-#pragma unroll
-      for (int i = 1; i < 4; i++) {
-#pragma unroll
-        for (int c = 0; c < NC; c++) t[c] = G::step(c, t[c]);
-        o[i] = lj_conv<G, F32>(G::out(t));
+    for (int c = 0; c < NC; c++) jrow[c] = G::mul(c, jrow[c], jstep[c]);
+  }
+}
+
+// Batched fills of GGL and RANECU handles: a warp pops an item (up to 8
+// streams of one request) and fills its streams one after the other.
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_batch_mlcg(const BatchQueue q) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const uint32_t it = pop_warp(q.counter);
+    if (it >= q.n_items) break;
+    const BatchItem I = q.items[it];
+    const BatchReq& r = q.reqs[I.req];
+    const FillDesc& d = r.d;
+    if (r.gen == GGL) {
+      LjConst<GglLJ> K;
+      K.init(lane, d.n_per);
+      for (uint32_t k = 0; k < I.rows; k++) {
+        if (d.f32) lj_stream<GglLJ, true>(K, d, I.row0 + k, lane);
+        else lj_stream<GglLJ, false>(K, d, I.row0 + k, lane);
       }
-      if (vec && c0 + 128 <= nv) {
-        st_out4(orow + c0, make_uint4(o[0], o[1], o[2], o[3]));
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-          if (c0 + 4 * lane + i < nv) st_out(orow + c0 + i, o[i]);
+    } else {
+      LjConst<RanecuLJ> K;
+      K.init(lane, d.n_per);
+      for (uint32_t k = 0; k < I.rows; k++) {
+        if (d.f32) lj_stream<RanecuLJ, true>(K, d, I.row0 + k, lane);
+        else lj_stream<RanecuLJ, false>(K, d, I.row0 + k, lane);
       }
-#pragma unroll
-      for (int c = 0; c < NC; c++) s[c] = G::mul(c, s[c], block_mul[c]);
-    }
-    if (!d.jump && lane == 0) {
-#pragma unroll
-      for (int c = 0; c < NC; c++) d.state[c * d.n_rows + row] = G::mul(c, base[c], fin_mul[c]);
-    }
-    if (d.jump) {
-#pragma unroll
-      for (int c = 0; c < NC; c++) jrow[c] = G::mul(c, jrow[c], jstep[c]);
     }
   }
 }
 
-static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 1;
-  }
-  return n;
+cudaError_t launch_batch_mlcg(const BatchQueue& q, Tile t, cudaStream_t s) {
+  (void)t;
+  if (q.n_items == 0) return cudaSuccess;
+  const uint32_t cap = (uint32_t)sm_count() * (2048 / 128);
+  const uint32_t need = (q.n_items + 3) / 4;
+  k_batch_mlcg<4><<<need < cap ? need : cap, 128, 0, s>>>(q);
+  return cudaGetLastError();
 }
 
 template <class G, int WPB, bool F32>

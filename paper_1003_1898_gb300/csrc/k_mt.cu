@@ -9,7 +9,7 @@
 // __syncwarp between its reads and its writes.  Each new word is tempered
 // and stored by the lane that produced it: 32 lanes x 4 words are 512
 // consecutive bytes of the stream's row, written without staging.
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -90,13 +90,9 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
   }
 }
 
-template <int WPB, bool F32>
-__global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
-  __shared__ __align__(16) uint32_t table[WPB][624];
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const uint64_t row = (uint64_t)blockIdx.x * WPB + wi;
-  if (row >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
-  uint32_t* s = table[wi];
+// Stream `row` of a fill by one warp; s is the warp's 624-word table.
+template <bool F32>
+__device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane) {
   uint32_t* gs = d.state + row * 624;
   for (int k = lane; k < 624; k += 32) s[k] = gs[k];
   __syncwarp();
@@ -105,22 +101,67 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
   const bool store = out != nullptr;
   uint32_t* orow = store ? out + row * d.pitch : nullptr;
   const uint64_t n = d.n_per;
+  // Draws of this row that are written (all n unless the element limit cuts
+  // the row); the stream still advances by n.
+  uint64_t nv = n;
+  if (store && d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
   uint64_t j = 0;
   const uint32_t mti = d.pos;
   if (mti < 624 && n > 0) {  // rest of the current table
     const uint64_t h = (624 - mti) < n ? (624 - mti) : n;
     if (store)
-      for (uint64_t k = lane; k < h; k += 32) st_out(orow + k, mt_conv<F32>(mt_temper(s[mti + k])));
+      for (uint64_t k = lane; k < h && k < nv; k += 32)
+        st_out(orow + k, mt_conv<F32>(mt_temper(s[mti + k])));
     j = h;
   }
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   const bool vec = store && ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   while (n - j >= 624) {
-    mt_twist<F32, false>(s, lane, store ? orow + j : nullptr, 624, vec);
+    if (j + 624 <= nv) mt_twist<F32, false>(s, lane, store ? orow + j : nullptr, 624, vec);
+    else mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false);
     j += 624;
   }
-  if (j < n) mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)(n - j), false);
+  if (j < n) {
+    const uint64_t take = nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
+    mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)take, false);
+  }
   for (int k = lane; k < 624; k += 32) gs[k] = s[k];
+  __syncwarp();
+}
+
+template <int WPB, bool F32>
+__global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
+  __shared__ __align__(16) uint32_t table[WPB][624];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const uint64_t row = (uint64_t)blockIdx.x * WPB + wi;
+  if (row >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
+  mt_stream<F32>(d, row, table[wi], lane);
+}
+
+// Batched MT19937 fills: each warp pops an item (up to 2 streams of one
+// request) and fills them one after the other in its own table.
+template <int WPB, bool F32>
+__global__ void __launch_bounds__(WPB * 32) k_batch_mt(const BatchQueue q) {
+  __shared__ __align__(16) uint32_t table[WPB][624];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  for (;;) {
+    const uint32_t it = pop_warp(q.counter);
+    if (it >= q.n_items) break;
+    const BatchItem I = q.items[it];
+    const FillDesc& d = q.reqs[I.req].d;
+    for (uint32_t k = 0; k < I.rows; k++) mt_stream<F32>(d, I.row0 + k, table[wi], lane);
+  }
+}
+
+cudaError_t launch_batch_mt(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
+  (void)t;
+  if (q.n_items == 0) return cudaSuccess;
+  const uint32_t cap = (uint32_t)sm_count() * (2048 / 256);
+  const uint32_t need = (q.n_items + 7) / 8;
+  const uint32_t grid = need < cap ? need : cap;
+  if (f32) k_batch_mt<8, true><<<grid, 256, 0, s>>>(q);
+  else k_batch_mt<8, false><<<grid, 256, 0, s>>>(q);
+  return cudaGetLastError();
 }
 
 template <int WPB, bool F32>

@@ -18,7 +18,7 @@
 // Delivered draws are staged in a column-major shared tile (see ColFlusher)
 // and written out 16 bytes at a time, so the stream-major HBM writes are
 // contiguous runs of each row.
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -132,20 +132,20 @@ __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int
   return ph;
 }
 
-template <int T, int KT, int P, bool F32>
-__global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
+// Streams [row0, row0 + T) of a fill, one per thread; smem holds KT
+// columns of T + 1 words.
+template <int T, int KT, int P, bool F32, bool LIMITED>
+__device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
   static_assert(KT >= 48, "the tile must hold a partial block next to the 24-word scratch ring");
   constexpr int SP = T + 1;
-  extern __shared__ uint32_t smem[];          // KT columns of SP words
   const int tid = threadIdx.x;
-  const uint64_t row0 = (uint64_t)blockIdx.x * T;
   const uint64_t row = row0 + tid;
   const bool active = row < d.n_rows;
   const uint64_t nr = d.n_rows;
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  ColFlusher<T> fl;
-  fl.init(smem, out, d.pitch, row0, nr);
+  ColFlusher<T, LIMITED> fl;
+  fl.init(smem, out, d.pitch, row0, nr, d.limit);
   uint32_t* col = smem + tid;                 // this thread's row of the tile (stride SP)
   uint32_t* ring = smem + 24 * SP + tid;      // scratch ring in tile columns 24..47
 
@@ -232,6 +232,61 @@ __global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
     for (int jj = 0; jj < 24; jj++) d.state[jj * nr + row] = R[jj] >> 8;
     d.state[24 * nr + row] = c;
   }
+}
+
+template <int T, int KT, int P, bool F32>
+__global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
+  extern __shared__ uint32_t smem[];
+  ranlux_rows<T, KT, P, F32, false>(d, (uint64_t)blockIdx.x * T, smem);
+}
+
+// Batched RANLUX fills of luxury P: a block pops an item (T streams).
+template <int T, int KT, int P, bool F32>
+__global__ void __launch_bounds__(T, 896 / T) k_batch_ranlux(const BatchQueue q) {
+  extern __shared__ uint32_t smem[];
+  __shared__ uint32_t slot;
+  for (;;) {
+    const uint32_t it = pop_cta(q.counter, &slot);
+    if (it >= q.n_items) break;
+    const BatchItem si = q.items[it];
+    const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
+    ranlux_rows<T, KT, P, F32, true>(sd, si.row0, smem);
+  }
+}
+
+template <int T, int KT, int P, bool F32>
+static cudaError_t launch_bl(const BatchQueue& q, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)KT * (T + 1) * sizeof(uint32_t);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_ranlux<T, KT, P, F32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_ranlux<T, KT, P, F32>, T, bytes);
+  const uint32_t cap = (uint32_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  k_batch_ranlux<T, KT, P, F32><<<q.n_items < cap ? q.n_items : cap, T, bytes, s>>>(q);
+  return cudaGetLastError();
+}
+
+template <int T, bool F32>
+static cudaError_t launch_bl_p(const BatchQueue& q, int p, cudaStream_t s) {
+  switch (p) {
+    case 24: return launch_bl<T, 48, 24, F32>(q, s);
+    case 48: return launch_bl<T, 48, 48, F32>(q, s);
+    case 97: return launch_bl<T, 48, 97, F32>(q, s);
+    case 223: return launch_bl<T, 48, 223, F32>(q, s);
+    case 389: return launch_bl<T, 48, 389, F32>(q, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_batch_ranlux(const BatchQueue& q, int p, Tile t, bool f32, cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  if (t.threads == 64) return f32 ? launch_bl_p<64, true>(q, p, s) : launch_bl_p<64, false>(q, p, s);
+  return f32 ? launch_bl_p<128, true>(q, p, s) : launch_bl_p<128, false>(q, p, s);
 }
 
 template <int T, int KT, int P, bool F32>

@@ -12,7 +12,7 @@
 // per draw as an offset of the block's entry value by a compile-time
 // constant, so no draw waits on the previous one.  Each block's 97 draws are staged in a column-major shared
 // tile and written out 16 bytes at a time (ColFlusher).
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -52,12 +52,12 @@ __device__ __forceinline__ uint32_t rm_conv(uint32_t x) {
   else return x;
 }
 
-template <int T, bool F32>
-__global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
-  constexpr int SP = T + 1;   // column-major tile of one 97-draw block (see ColFlusher)
-  extern __shared__ uint32_t smem[];
+// Streams [row0, row0 + T) of a fill, one per thread; smem holds one
+// column-major tile of 97 columns (see ColFlusher).
+template <int T, bool F32, bool LIMITED>
+__device__ __forceinline__ void ranmar_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
+  constexpr int SP = T + 1;
   const int tid = threadIdx.x;
-  const uint64_t row0 = (uint64_t)blockIdx.x * T;
   const uint64_t row = row0 + tid;
   const bool active = row < d.n_rows;
   const uint64_t nr = d.n_rows;
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
 
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  ColFlusher<T> fl;
-  fl.init(smem, out, d.pitch, row0, nr);
+  ColFlusher<T, LIMITED> fl;
+  fl.init(smem, out, d.pitch, row0, nr, d.limit);
   uint32_t* col = smem + tid;
   const uint64_t n = d.n_per;
   const uint64_t nfull = n / 97;
@@ -121,6 +121,43 @@ __global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
     }
     d.state[97 * nr + row] = C;
   }
+}
+
+template <int T, bool F32>
+__global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
+  extern __shared__ uint32_t smem[];
+  ranmar_rows<T, F32, false>(d, (uint64_t)blockIdx.x * T, smem);
+}
+
+// Batched RANMAR fills: one block per item (T streams of one request),
+// items ordered longest first.  With the 97-word lag table in registers a
+// persistent loop around the body does not fit the register budget, so
+// here the hardware block scheduler hands out the items in order.
+template <int T, bool F32>
+__global__ void __launch_bounds__(T, 512 / T) k_batch_ranmar(const BatchQueue q) {
+  extern __shared__ uint32_t smem[];
+  const BatchItem si = q.items[blockIdx.x];
+  ranmar_rows<T, F32, true>(q.reqs[si.req].d, si.row0, smem);
+}
+
+template <int T, bool F32>
+static cudaError_t launch_bm(const BatchQueue& q, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)97 * (T + 1) * sizeof(uint32_t);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_ranmar<T, F32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_batch_ranmar<T, F32><<<q.n_items, T, bytes, s>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ranmar(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  if (t.threads == 128) return f32 ? launch_bm<128, true>(q, s) : launch_bm<128, false>(q, s);
+  return f32 ? launch_bm<64, true>(q, s) : launch_bm<64, false>(q, s);
 }
 
 template <int T, bool F32>

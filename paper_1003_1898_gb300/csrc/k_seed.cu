@@ -10,7 +10,7 @@
 //   RANLUX   24 words from the MLCG 40014 mod 2147483563 started at
 //            s mod 2147483563 (19780503 when that is 0), carry = (x_{-1} == 0)
 //   MT19937  init_genrand(lo32(s))
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -43,9 +43,8 @@ __device__ void rmarin_to_state(uint32_t ij, uint32_t kl, uint32_t* st, uint64_t
   st[97 * n + row] = 362436u;  // C_0 = 362436 / 2^24
 }
 
-__global__ void k_seed(int gen, uint64_t seed, uint64_t n, uint32_t* st) {
-  const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
+// Seed stream `row` of a handle of n streams (state layout in common.cuh).
+__device__ void seed_stream(int gen, uint64_t seed, uint64_t n, uint32_t* st, uint64_t row) {
   const uint64_t s = splitmix64(seed + row);
   const uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32);
   switch (gen) {
@@ -92,6 +91,41 @@ __global__ void k_seed(int gen, uint64_t seed, uint64_t n, uint32_t* st) {
       break;
     }
   }
+}
+
+__global__ void k_seed(int gen, uint64_t seed, uint64_t n, uint32_t* st) {
+  const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < n) seed_stream(gen, seed, n, st, row);
+}
+
+// Persistent seeding of every re-seeded request of a batch: an item is up
+// to 256 consecutive streams of one request.
+__global__ void __launch_bounds__(256) k_batch_seed(const BatchQueue q) {
+  __shared__ uint32_t slot;
+  for (;;) {
+    const uint32_t it = pop_cta(q.counter, &slot);
+    if (it >= q.n_items) break;
+    const BatchItem I = q.items[it];
+    const BatchReq& r = q.reqs[I.req];
+    if (threadIdx.x < I.rows) seed_stream(r.gen, r.seed, r.d.n_rows, r.d.state, I.row0 + threadIdx.x);
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    n = (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 1;
+  }
+  return n;
+}
+
+cudaError_t launch_batch_seed(const BatchQueue& q, cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  const uint32_t cap = (uint32_t)sm_count() * 8;
+  k_batch_seed<<<q.n_items < cap ? q.n_items : cap, 256, 0, s>>>(q);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_seed(int gen, int p, uint64_t seed, uint64_t n, uint32_t* state, cudaStream_t s) {

@@ -13,7 +13,7 @@
 // tiles one barrier per tile suffices; S = 1 halves the shared memory per
 // stream (two barriers per tile) so that every stream of a large handle can
 // be resident at once instead of running a partial second wave.
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace prng {
 
@@ -94,15 +94,15 @@ __device__ __forceinline__ uint32_t conv(uint32_t v) {
 template <int K>
 __device__ __forceinline__ int swz(int row, int ch) { return ch ^ (row & 7); }
 
+// Streams [row0, row0 + T) of a fill, one per thread; smem holds S tiles of
+// T * K words.
 template <class G, int T, int K, int S, bool F32>
-__global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
+__device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
   static_assert(K % 32 == 0, "tile rows hold whole 8-chunk swizzle groups");
   constexpr int CH = K / 4;          // 16-byte chunks per row
   constexpr int RS = T / CH;         // rows one copy-out pass of the CTA covers
   static_assert(RS % 8 == 0, "copy-out rows of one thread must share a swizzle phase");
-  extern __shared__ __align__(16) uint32_t smem[];  // S tiles of T * K words
   const int tid = threadIdx.x;
-  const uint64_t row0 = (uint64_t)blockIdx.x * T;
   const uint64_t row = row0 + tid;
   const bool active = row < d.n_rows;
 
@@ -166,6 +166,56 @@ __global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
     else buf ^= 1;
   }
   if (active) g.store(d.state, d.n_rows, row);
+}
+
+template <class G, int T, int K, int S, bool F32>
+__global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  simple_rows<G, T, K, S, F32>(d, (uint64_t)blockIdx.x * T, smem);
+}
+
+// Batched XOR128 fills: a block pops an item (T streams of one request).
+template <int T, int K, int S, bool F32>
+__global__ void __launch_bounds__(T) k_batch_xor128(const BatchQueue q) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t slot;
+  for (;;) {
+    const uint32_t it = pop_cta(q.counter, &slot);
+    if (it >= q.n_items) break;
+    const BatchItem si = q.items[it];
+    const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
+    simple_rows<Xor128Gen, T, K, S, F32>(sd, si.row0, smem);
+  }
+}
+
+template <int T, int K, int S, bool F32>
+static cudaError_t launch_bx(const BatchQueue& q, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)S * T * K * sizeof(uint32_t);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_xor128<T, K, S, F32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_xor128<T, K, S, F32>, T, bytes);
+  const uint32_t cap = (uint32_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  k_batch_xor128<T, K, S, F32><<<q.n_items < cap ? q.n_items : cap, T, bytes, s>>>(q);
+  return cudaGetLastError();
+}
+
+template <int T, int K, int S>
+static cudaError_t launch_bx2(const BatchQueue& q, bool f32, cudaStream_t s) {
+  return f32 ? launch_bx<T, K, S, true>(q, s) : launch_bx<T, K, S, false>(q, s);
+}
+
+cudaError_t launch_batch_xor128(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
+  if (q.n_items == 0) return cudaSuccess;
+  if (t.threads == 128 && t.cols == 32 && t.stages == 2) return launch_bx2<128, 32, 2>(q, f32, s);
+  if (t.threads == 128 && t.cols == 64 && t.stages == 1) return launch_bx2<128, 64, 1>(q, f32, s);
+  if (t.threads == 256 && t.cols == 32 && t.stages == 1) return launch_bx2<256, 32, 1>(q, f32, s);
+  return launch_bx2<128, 32, 1>(q, f32, s);
 }
 
 // Skip without output for XOR128 (plain stepping).

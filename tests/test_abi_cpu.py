@@ -75,3 +75,15 @@ def test_strerror_names_every_code(L):
         s = P.prng_strerror(code)
         assert s and s != "unknown error code"
     assert P.prng_strerror(-99) == "unknown error code"
+
+
+def test_batch_create_rejects_bad_arguments(L):
+    b = ctypes.c_void_p()
+    assert L.prng_batch_create(None, None, 1) == -4
+    assert L.prng_batch_create(ctypes.byref(b), None, 0) == -3
+    assert L.prng_batch_create(ctypes.byref(b), None, 3) == -4
+    reqs = (P.PrngFillReq * 1)()          # st = NULL
+    assert L.prng_batch_create(ctypes.byref(b), reqs, 1) == -4
+    assert L.prng_batch_launch(None, None) == -4
+    assert L.prng_batch_info(None, None, None, None) == -4
+    L.prng_batch_destroy(None)
