@@ -52,7 +52,8 @@ enum {
   PRNG_ECUDA = -6,       /* a CUDA call or launch failed                         */
   PRNG_EUNSUPPORTED = -7,/* operation not defined for this generator             */
   PRNG_EBLOB = -8,       /* malformed or mismatched state blob                   */
-  PRNG_ESEED = -9        /* jump start value outside the generator's range       */
+  PRNG_ESEED = -9,       /* jump start value outside the generator's range       */
+  PRNG_ESCRATCH = -10    /* batch larger than prng_batch_fill_noalloc's fixed scratch */
 };
 
 /* Opaque handle: one generator type, n_streams independent streams, their
@@ -155,6 +156,35 @@ int prng_batch_info(const prng_batch *b, uint32_t *n_requests, uint64_t *n_items
 
 /* Wait for the batch's launches and free it (NULL accepted). */
 void prng_batch_destroy(prng_batch *b);
+
+/* Batched fill that allocates nothing (no counterpart in the paper; a
+ * service of this library).  It is meant for callers that must not let a
+ * library allocate device memory: code running under a framework's caching
+ * allocator, services that reserve all device memory up front, and loops
+ * that cannot afford the synchronisation an allocation may imply.  It does
+ * what prng_batch_create + one prng_batch_launch + prng_batch_destroy do
+ * for the same requests -- the same draws, the same handle advance -- but
+ * its descriptors, work items and work counters live in one fixed device
+ * array inside the library (about 2.4 MB, held on every device that loads
+ * the library until the process exits), staged through a fixed host
+ * buffer, and its kernels run one after the other on `stream`.
+ *   - At most PRNG_NOALLOC_MAX_REQUESTS requests and PRNG_NOALLOC_MAX_ITEMS
+ *     work items (streams / 256 per re-seeded request plus, per fill, its
+ *     streams / 4 for GGL and RANECU, / 2 for MT19937, / the tile width
+ *     otherwise); larger batches return PRNG_ESCRATCH and launch nothing.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the array and the previous call's contents remain
+ *     there (the work counters are cleared at the start of each call): two
+ *     calls whose work overlaps on the GPU -- for example calls on two
+ *     streams that nothing orders -- race and give wrong output.  Host
+ *     threads are serialised by a lock around the host-side staging.
+ *   - The host copy of the descriptors is pageable: the call returns once
+ *     it has been handed to the device copy engine, which may wait for
+ *     `stream` to drain first. */
+#define PRNG_NOALLOC_MAX_REQUESTS 4096u
+#define PRNG_NOALLOC_MAX_ITEMS 131072u
+int prng_batch_fill_noalloc(const prng_fill_req *reqs, uint32_t n_reqs, void *stream);
 
 /* Launch tile used by fills of generator `gen` (for RANLUX: of luxury p)
  * on this process: threads per CTA, staged draws per thread per tile

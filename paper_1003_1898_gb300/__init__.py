@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         "prng_batch_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u64)],
                             ctypes.c_int),
         "prng_batch_destroy": ([vp], None),
+        "prng_batch_fill_noalloc": ([ctypes.POINTER(PrngFillReq), u32, vp], ctypes.c_int),
         "prng_destroy": ([vp], None),
         "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -172,11 +173,9 @@ def prng_get_tile(gen, luxury: int = 0):
     return (t.value, c.value, s.value)
 
 
-def prng_batch_create(reqs) -> ctypes.c_void_p:
-    """reqs: iterable of dicts with keys st, d_out, n_per_stream and optional
-    n_valid, seed, f32, reseed."""
+def _fill_req_array(reqs):
     reqs = list(reqs)
-    arr = (PrngFillReq * len(reqs))()
+    arr = (PrngFillReq * max(1, len(reqs)))()
     for i, r in enumerate(reqs):
         st = r["st"]
         arr[i].st = st.value if isinstance(st, ctypes.c_void_p) else st
@@ -186,9 +185,23 @@ def prng_batch_create(reqs) -> ctypes.c_void_p:
         arr[i].seed = r.get("seed", 0) & (2**64 - 1)
         arr[i].f32 = 1 if r.get("f32", False) else 0
         arr[i].reseed = 1 if r.get("reseed", False) else 0
+    return arr, len(reqs)
+
+
+def prng_batch_create(reqs) -> ctypes.c_void_p:
+    """reqs: iterable of dicts with keys st, d_out, n_per_stream and optional
+    n_valid, seed, f32, reseed."""
+    arr, n = _fill_req_array(reqs)
     b = ctypes.c_void_p()
-    _check(lib().prng_batch_create(ctypes.byref(b), arr, len(reqs)), "prng_batch_create")
+    _check(lib().prng_batch_create(ctypes.byref(b), arr, n), "prng_batch_create")
     return b
+
+
+def prng_batch_fill_noalloc(reqs, stream=None):
+    """The batched fill through the library's fixed scratch (allocates
+    nothing); same request dicts as prng_batch_create."""
+    arr, n = _fill_req_array(reqs)
+    _check(lib().prng_batch_fill_noalloc(arr, n, _stream(stream)), "prng_batch_fill_noalloc")
 
 
 def prng_batch_launch(b, stream=None):

@@ -339,6 +339,7 @@ const char* prng_strerror(int code) {
     case PRNG_EUNSUPPORTED: return "operation not supported for this generator";
     case PRNG_EBLOB: return "state blob does not match this handle";
     case PRNG_ESEED: return "start value outside the generator's range";
+    case PRNG_ESCRATCH: return "batch exceeds the fixed scratch of prng_batch_fill_noalloc";
     default: return "unknown error code";
   }
 }
