@@ -78,6 +78,15 @@ def lib():
             L.orc_serial_fill.argtypes = [i32, u64, u64, vp]
             L.orc_explicit_draws.restype = ctypes.c_int
             L.orc_explicit_draws.argtypes = [i32, i32, vp, u32, u64, vp]
+            L.orc_ising_half_sweep.restype = None
+            L.orc_ising_half_sweep.argtypes = [i32, vp, vp, i32, u32, u32, i32]
+            L.orc_ising_thresholds.restype = None
+            L.orc_ising_thresholds.argtypes = [ctypes.c_double, ctypes.POINTER(u32),
+                                               ctypes.POINTER(u32)]
+            L.orc_ising_energy.restype = ctypes.c_int64
+            L.orc_ising_energy.argtypes = [i32, vp]
+            L.orc_ising_magnetisation.restype = ctypes.c_int64
+            L.orc_ising_magnetisation.argtypes = [i32, vp]
             L.orc_checksum_draws.restype = u64
             L.orc_checksum_draws.argtypes = [i32, i32, u64, u64, u64]
             L.orc_luxury_p.restype = i32
@@ -185,3 +194,52 @@ def ranecu_components(s1: int, s2: int, n: int):
     c1 = np.array([L.orc_ranecu_comp1(ctypes.byref(a)) for _ in range(n)], dtype=np.uint32)
     c2 = np.array([L.orc_ranecu_comp2(ctypes.byref(b)) for _ in range(n)], dtype=np.uint32)
     return c1, c2
+
+
+# ---------------------------------------------------------------- Ising consumer
+
+ISING_BETA = 0.4406868
+
+
+def ising_thresholds(beta: float = ISING_BETA):
+    t4, t8 = ctypes.c_uint32(), ctypes.c_uint32()
+    lib().orc_ising_thresholds(beta, ctypes.byref(t4), ctypes.byref(t8))
+    return int(t4.value), int(t8.value)
+
+
+def ising_half_sweep(spins, draws, gen, colour: int, t4: int, t8: int):
+    """In place on an (L, L) int8 array; draws: L*L/2 uint32 (stream-major fill)."""
+    L = spins.shape[0]
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous
+    d = np.ascontiguousarray(draws, dtype=np.uint32).reshape(-1)
+    assert d.shape[0] == L * L // 2
+    lib().orc_ising_half_sweep(L, spins.ctypes.data, d.ctypes.data, SHIFT[gen_id(gen)], t4, t8,
+                               colour)
+
+
+def ising_energy(spins) -> int:
+    return int(lib().orc_ising_energy(spins.shape[0], spins.ctypes.data))
+
+
+def ising_magnetisation(spins) -> int:
+    return int(lib().orc_ising_magnetisation(spins.shape[0], spins.ctypes.data))
+
+
+def ising_run(gen, seed: int, n_streams: int, L: int, sweeps: int, *, luxury: int = 0,
+              beta: float = ISING_BETA, skip: int = 0, spins=None):
+    """Cold start (all +1) unless spins is given; each half-sweep takes the
+    next L*L/(2 n_streams) draws of every stream of the handle (after `skip`
+    draws per stream).  Returns the lattice and the (E, M) after every
+    sweep."""
+    t4, t8 = ising_thresholds(beta)
+    s = np.ones((L, L), dtype=np.int8) if spins is None else spins.copy()
+    per = L * L // (2 * n_streams)
+    assert per * 2 * n_streams == L * L
+    all_draws = fill(gen, seed, n_streams, 2 * sweeps * per, luxury=luxury, skip=skip)
+    em = []
+    for sw in range(sweeps):
+        for colour in (0, 1):
+            h = 2 * sw + colour
+            ising_half_sweep(s, all_draws[:, h * per:(h + 1) * per], gen, colour, t4, t8)
+        em.append((ising_energy(s), ising_magnetisation(s)))
+    return s, em

@@ -34,6 +34,7 @@
  */
 #include "prng_oracle.h"
 
+#include <math.h>
 #include <stddef.h>
 #include <string.h>
 
@@ -469,6 +470,52 @@ int orc_serial_fill(int32_t gen, uint64_t x0, uint64_t n, uint32_t *out_u32) {
   if (orc_serial_start(&st, gen, x0) != 0) return -1;
   for (uint64_t j = 0; j < n; j++) out_u32[j] = orc_stream_next(&st);
   return 0;
+}
+
+/* ---------------------------------------------------------------- Ising */
+
+void orc_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8) {
+  *t4 = (uint32_t)floor(16777216.0 * exp(-4.0 * beta));
+  *t8 = (uint32_t)floor(16777216.0 * exp(-8.0 * beta));
+}
+
+void orc_ising_half_sweep(int32_t L, int8_t *spins, const uint32_t *draws, int32_t shift,
+                          uint32_t t4, uint32_t t8, int32_t colour) {
+  for (int32_t y = 0; y < L; y++) {
+    for (int32_t x = 0; x < L; x++) {
+      if ((x + y) % 2 != colour) continue;
+      int32_t k = y * (L / 2) + x / 2;
+      int32_t s = spins[y * L + x];
+      int32_t up = spins[((y + L - 1) % L) * L + x];
+      int32_t down = spins[((y + 1) % L) * L + x];
+      int32_t left = spins[y * L + (x + L - 1) % L];
+      int32_t right = spins[y * L + (x + 1) % L];
+      int32_t dE = 2 * s * (up + down + left + right);
+      uint32_t r = draws[k] >> shift;
+      int accept;
+      if (dE <= 0) accept = 1;
+      else if (dE == 4) accept = r < t4;
+      else accept = r < t8;
+      if (accept) spins[y * L + x] = (int8_t)(-s);
+    }
+  }
+}
+
+int64_t orc_ising_energy(int32_t L, const int8_t *spins) {
+  int64_t e = 0;
+  for (int32_t y = 0; y < L; y++)
+    for (int32_t x = 0; x < L; x++) {
+      int32_t s = spins[y * L + x];
+      e -= s * spins[y * L + (x + 1) % L];
+      e -= s * spins[((y + 1) % L) * L + x];
+    }
+  return e;
+}
+
+int64_t orc_ising_magnetisation(int32_t L, const int8_t *spins) {
+  int64_t m = 0;
+  for (int64_t i = 0; i < (int64_t)L * L; i++) m += spins[i];
+  return m;
 }
 
 /* ---------------------------------------------------------------- timing */

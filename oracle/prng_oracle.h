@@ -117,6 +117,24 @@ int orc_serial_sample(int32_t gen, uint64_t x0, const uint64_t *pos,
 /* Same sequence, the first n draws, written in full. */
 int orc_serial_fill(int32_t gen, uint64_t x0, uint64_t n, uint32_t *out_u32);
 
+/* ------------------------------------------------------------ Ising consumer
+ * Checkerboard Metropolis half-sweep of the periodic L x L Ising model
+ * (J = 1, h = 0), the Monte Carlo use the paper's generators serve (Section
+ * 3.5 cites RANMAR's earlier use for Ising simulations).  Spins are +1/-1 in
+ * int8, row-major.  Only sites of colour `colour` ((x + y) % 2) are
+ * visited; the site with colour rank k (row-major order among sites of that
+ * colour, k = y L/2 + x/2) uses draw draws[k], whose 24-bit value
+ * r = draws[k] >> shift is compared with the integer thresholds:
+ * the flip is accepted when dE = 2 s (sum of the 4 neighbours) <= 0, or
+ * when r < t4 (dE = 4) or r < t8 (dE = 8).  L must be even. */
+void orc_ising_half_sweep(int32_t L, int8_t *spins, const uint32_t *draws, int32_t shift,
+                          uint32_t t4, uint32_t t8, int32_t colour);
+/* floor(2^24 exp(-dE beta)) for dE = 4 and 8, evaluated in double. */
+void orc_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8);
+/* E = -sum over nearest-neighbour bonds of s_i s_j (each bond once). */
+int64_t orc_ising_energy(int32_t L, const int8_t *spins);
+int64_t orc_ising_magnetisation(int32_t L, const int8_t *spins);
+
 /* Timing helper for the CPU baseline: draws n values from one stream and
  * returns a running checksum so the work cannot be optimised away. */
 uint64_t orc_checksum_draws(int32_t gen, int32_t luxury, uint64_t seed,
