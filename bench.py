@@ -335,6 +335,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         batched = measure_batched(P, dev, args)
 
+    # Serving loop (512 clients, Poisson arrivals, fills and Ising runs):
+    # continuous batching vs a plain one-request-at-a-time queue.
+    serving = None
+    if not args.no_serving:
+        serving = measure_serving(args)
+
     # end-to-end through the public API with host buffers: fill, then copy
     # every output to pinned host memory inside the timed region.
     e2e = None
@@ -362,6 +368,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched": batched,
+        "serving": serving,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -456,6 +463,37 @@ def measure_batched(P, dev, args):
                     "enqueue time of its launches"}
 
 
+def measure_serving(args):
+    """512 clients with device-resident streams (half RANLUX p = 223), Poisson
+    arrivals at each rate, requests 50/50 a fill of 1e3..1e6 numbers or 16
+    checkerboard sweeps of an L x L Ising lattice (L in {256, 1024, 4096}),
+    40 GB state + output cap.  Aggregate numbers/s counts every draw served
+    (fill outputs and Ising draws)."""
+    from paper_1003_1898_gb300 import serve as S
+    from paper_1003_1898_gb300 import workloads as W
+    specs = W.serving_clients(W.SERVE_CLIENTS)
+    out = {"clients": W.SERVE_CLIENTS, "streams_per_client": W.SERVE_STREAMS,
+           "mem_cap_bytes": W.SERVE_MEM_CAP, "rates": []}
+    for rate in args.serve_rates:
+        row = {"rate_per_s": rate, "requests": args.serve_requests}
+        for mode, max_active in (("continuous", 0), ("queue", 1)):
+            if mode == "queue" and rate != args.serve_rates[0]:
+                continue
+            raw = W.serving_requests(args.serve_requests, rate)
+            reqs = [S.Request(**r) for r in raw]
+            srv = S.Server(specs, n_streams=W.SERVE_STREAMS, mem_cap=W.SERVE_MEM_CAP,
+                           max_active=max_active)
+            try:
+                srv.run(reqs[: min(50, len(reqs))], realtime=False)   # warm-up (compile, caches)
+                reqs = [S.Request(**r) for r in raw]
+                done = srv.run(reqs, realtime=True)
+            finally:
+                srv.close()
+            row[mode] = S.latency_stats(done)
+        out["rates"].append(row)
+    return out
+
+
 def measure_e2e(P, handles, seed_r, items, dev, args):
     import torch
     stream = torch.cuda.current_stream()
@@ -516,6 +554,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=20000)
     ap.add_argument("--batch-passes", type=int, default=3)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 4000.0, 16000.0])
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

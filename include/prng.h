@@ -157,6 +157,49 @@ int prng_batch_info(const prng_batch *b, uint32_t *n_requests, uint64_t *n_items
 /* Wait for the batch's launches and free it (NULL accepted). */
 void prng_batch_destroy(prng_batch *b);
 
+/* A batched-fill engine for request sets that change from launch to launch
+ * (a serving loop's ticks).  It owns a ring of staging slots, each sized for
+ * max_requests requests and max_items work items (work items as for
+ * prng_batch_create).  prng_batcher_launch plans the given requests into
+ * the next slot, copies them to the device and launches the same family
+ * kernels as a batch, on `stream`, asynchronously; a slot is reused once the
+ * launch that last used it has completed (the call waits for that on the
+ * host).  Each handle at most once per launch; handles advance as after
+ * their own fills.  PRNG_ESIZE when a launch exceeds the slot size. */
+typedef struct prng_batcher prng_batcher;
+int prng_batcher_create(prng_batcher **out, uint32_t max_requests, uint64_t max_items);
+int prng_batcher_launch(prng_batcher *b, const prng_fill_req *reqs, uint32_t n_reqs, void *stream);
+void prng_batcher_destroy(prng_batcher *b);
+
+/* ---------------------------------------------------------------- Ising
+ * Checkerboard Metropolis half-sweeps of periodic 2-D Ising lattices (J = 1,
+ * h = 0) that consume the generators' draws -- the Monte Carlo use the
+ * paper's generators are built for (Section 3.5 cites RANMAR's Ising
+ * simulations).  Spins are +1/-1 in int8, row-major L x L, L even.  Only
+ * sites of colour `colour` ((x + y) % 2) are visited; the site of colour
+ * rank k (k = y L/2 + x/2) uses d_draws[k], whose 24-bit value
+ * r = d_draws[k] >> shift (shift = the generator's float shift: 7 for GGL
+ * and RANECU, 8 for XOR128 and MT19937, 0 for RANMAR and RANLUX) accepts
+ * the flip when dE = 2 s (sum of the four neighbours) <= 0, or when r < t4
+ * (dE = 4) or r < t8 (dE = 8).  d_draws is typically a handle's u32 fill of
+ * L*L/2 draws (stream-major). */
+typedef struct prng_ising_req {
+  int8_t *d_spins;
+  const uint32_t *d_draws;
+  uint32_t L;
+  uint32_t colour;
+  uint32_t shift;
+  uint32_t t4;
+  uint32_t t8;
+} prng_ising_req;
+
+/* One half-sweep of each of the n lattices, asynchronously on `stream`.
+ * The descriptors are passed by value to the kernels (no allocation). */
+int prng_ising_half_sweep(const prng_ising_req *reqs, uint32_t n, void *stream);
+
+/* t4 = floor(2^24 exp(-4 beta)), t8 = floor(2^24 exp(-8 beta)), in double. */
+int prng_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8);
+
 /* Batched fill that allocates nothing (no counterpart in the paper; a
  * service of this library).  It is meant for callers that must not let a
  * library allocate device memory: code running under a framework's caching

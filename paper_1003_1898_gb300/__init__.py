@@ -23,6 +23,13 @@ STATE_WORDS = (1, 4, 2, 98, 25, 624)
 _lib = None
 
 
+class PrngIsingReq(ctypes.Structure):
+    """struct prng_ising_req (include/prng.h)."""
+    _fields_ = [("d_spins", ctypes.c_void_p), ("d_draws", ctypes.c_void_p), ("L", ctypes.c_uint32),
+                ("colour", ctypes.c_uint32), ("shift", ctypes.c_uint32), ("t4", ctypes.c_uint32),
+                ("t8", ctypes.c_uint32)]
+
+
 class PrngFillReq(ctypes.Structure):
     """struct prng_fill_req (include/prng.h)."""
     _fields_ = [("st", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
@@ -67,6 +74,12 @@ def lib() -> ctypes.CDLL:
                             ctypes.c_int),
         "prng_batch_destroy": ([vp], None),
         "prng_batch_fill_noalloc": ([ctypes.POINTER(PrngFillReq), u32, vp], ctypes.c_int),
+        "prng_batcher_create": ([ctypes.POINTER(vp), u32, u64], ctypes.c_int),
+        "prng_batcher_launch": ([vp, ctypes.POINTER(PrngFillReq), u32, vp], ctypes.c_int),
+        "prng_batcher_destroy": ([vp], None),
+        "prng_ising_half_sweep": ([ctypes.POINTER(PrngIsingReq), u32, vp], ctypes.c_int),
+        "prng_ising_thresholds": ([ctypes.c_double, ctypes.POINTER(u32), ctypes.POINTER(u32)],
+                                  ctypes.c_int),
         "prng_destroy": ([vp], None),
         "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -217,6 +230,48 @@ def prng_batch_info(b) -> dict:
 
 def prng_batch_destroy(b):
     lib().prng_batch_destroy(b)
+
+
+def prng_batcher_create(max_requests: int, max_items: int) -> ctypes.c_void_p:
+    b = ctypes.c_void_p()
+    _check(lib().prng_batcher_create(ctypes.byref(b), max_requests, max_items),
+           "prng_batcher_create")
+    return b
+
+
+def prng_batcher_launch(b, reqs, stream=None):
+    arr, n = _fill_req_array(reqs)
+    _check(lib().prng_batcher_launch(b, arr, n, _stream(stream)), "prng_batcher_launch")
+
+
+def prng_batcher_destroy(b):
+    lib().prng_batcher_destroy(b)
+
+
+SHIFT = {GGL: 7, RANECU: 7, XOR128: 8, MT19937: 8, RANMAR: 0, RANLUX: 0}
+
+
+def prng_ising_thresholds(beta: float):
+    t4, t8 = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().prng_ising_thresholds(beta, ctypes.byref(t4), ctypes.byref(t8)),
+           "prng_ising_thresholds")
+    return t4.value, t8.value
+
+
+def prng_ising_half_sweep(reqs, stream=None):
+    """reqs: iterable of dicts with d_spins, d_draws, L, colour, gen (or
+    shift), t4, t8."""
+    reqs = list(reqs)
+    arr = (PrngIsingReq * max(1, len(reqs)))()
+    for i, r in enumerate(reqs):
+        arr[i].d_spins = _ptr(r["d_spins"])
+        arr[i].d_draws = _ptr(r["d_draws"])
+        arr[i].L = r["L"]
+        arr[i].colour = r["colour"]
+        arr[i].shift = r["shift"] if "shift" in r else SHIFT[_gen(r["gen"])]
+        arr[i].t4 = r["t4"]
+        arr[i].t8 = r["t8"]
+    _check(lib().prng_ising_half_sweep(arr, len(reqs), _stream(stream)), "prng_ising_half_sweep")
 
 
 def prng_destroy(h):

@@ -1,0 +1,245 @@
+"""Continuous-batching serving loop over device-resident client streams.
+
+Each client owns a handle (one generator, n_streams streams) whose state
+stays on the device between requests.  A request is either a fill of n
+numbers (the first n of the client's next stream-major block, n_per =
+ceil(n / n_streams) draws per stream) or an Ising run: `sweeps` checkerboard
+Metropolis sweeps of an L x L lattice (cold start), every half-sweep
+consuming the client's next L*L/2 draws (L*L/(2 n_streams) per stream).
+
+The loop works in ticks.  A tick admits arrived requests in arrival order
+while their client is free and the state-plus-output memory stays under the
+cap, advances every running Ising request by one half-sweep, and enqueues
+one batched fill (prng_batcher_launch: the new fills plus the draws of all
+running Ising half-sweeps) and one batched half-sweep
+(prng_ising_half_sweep) on the server's stream.  Up to `max_inflight` ticks
+are on the GPU while the host forms the next, so requests that arrive while
+others run join the next tick.  A client's requests are served in order and
+only its own requests touch its streams, so every result is the same as the
+client would get alone.  Latency = completion (the end event of the tick
+that finishes the request, on the device clock) - arrival.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+from . import (GEN_IDS, SHIFT, prng_batcher_create, prng_batcher_destroy, prng_batcher_launch,
+               prng_create, prng_destroy, prng_info, prng_ising_half_sweep, prng_ising_thresholds)
+
+ISING_BETA = 0.4406868
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    client: int
+    kind: str                  # "fill" or "ising"
+    arrival: float = 0.0       # seconds after the start of the run
+    n: int = 0                 # fill: numbers wanted
+    f32: bool = False          # fill: float output
+    L: int = 0                 # ising: lattice side
+    sweeps: int = 16           # ising: full sweeps
+    # filled in by the server
+    out: object = None         # fill output (CUDA tensor), kept when the server keeps results
+    spins: object = None       # ising lattice (CUDA int8 tensor)
+    draws: object = None
+    half_done: int = 0
+    done: float = None         # completion time, seconds after the start
+    numbers: int = 0           # draws this request consumed
+
+
+class Client:
+    def __init__(self, cid: int, gen, luxury: int, seed: int, n_streams: int):
+        self.cid = cid
+        self.gen = GEN_IDS[gen] if isinstance(gen, str) else int(gen)
+        self.luxury = luxury
+        self.n_streams = n_streams
+        self.handle = prng_create(self.gen, seed, n_streams, luxury)
+        self.state_bytes = prng_info(self.handle)["state_bytes"]
+        self.busy = None           # running Ising request
+
+    def close(self):
+        if self.handle is not None:
+            prng_destroy(self.handle)
+            self.handle = None
+
+
+class Server:
+    def __init__(self, client_specs, n_streams: int = 1024, mem_cap: float = 40e9,
+                 max_inflight: int = 2, beta: float = ISING_BETA, keep_results: bool = False,
+                 max_active: int = 0):
+        """max_active > 0 caps the requests in progress (1 = a plain FIFO queue,
+        one request at a time, the baseline continuous batching is measured
+        against)."""
+        import torch
+        self.torch = torch
+        self.clients = [Client(i, g, lux, seed, n_streams)
+                        for i, (g, lux, seed) in enumerate(client_specs)]
+        self.n_streams = n_streams
+        self.mem_cap = mem_cap
+        self.mem_state = sum(c.state_bytes for c in self.clients)
+        self.mem_used = self.mem_state
+        self.max_inflight = max_inflight
+        self.max_active = max_active
+        self.keep = keep_results
+        self.t4, self.t8 = prng_ising_thresholds(beta)
+        self.stream = torch.cuda.Stream()
+        # every client contributes at most one fill per tick; items per
+        # request are at most n_streams / 2 (MT19937 takes 2 streams per item)
+        self.batcher = prng_batcher_create(len(self.clients),
+                                           len(self.clients) * max(1, n_streams // 2) + 1024)
+
+    def close(self):
+        if self.batcher is not None:
+            self.stream.synchronize()
+            prng_batcher_destroy(self.batcher)
+            self.batcher = None
+        for c in self.clients:
+            c.close()
+
+    # ------------------------------------------------------------------ sizes
+    def _fill_shape(self, n):
+        per = -(-n // self.n_streams)
+        return per, self.n_streams * per
+
+    def _bytes(self, r: Request) -> int:
+        if r.kind == "fill":
+            return 4 * self._fill_shape(r.n)[1]
+        return r.L * r.L + 2 * r.L * r.L          # int8 lattice + L*L/2 u32 draws
+
+    # ------------------------------------------------------------------ run
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (sorted by arrival).  With realtime the loop
+        releases each request at its arrival time; otherwise all are
+        available at once.  Returns the requests with their completion
+        times."""
+        torch = self.torch
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in reqs:
+            if r.kind == "ising":
+                if r.L % 2 or (r.L * r.L) % (2 * self.n_streams):
+                    raise ValueError("L*L/2 must be a multiple of the client's stream count")
+            elif r.n <= 0:
+                raise ValueError("fill requests need n > 0")
+        pending = collections.deque()
+        inflight = collections.deque()         # (end event, [requests finishing])
+        nxt = 0
+        t_start = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(self.stream):
+            t_start.record(self.stream)
+        wall0 = time.perf_counter()
+        running = []                           # Ising requests in progress
+        left = len(reqs)
+
+        def retire(block: bool):
+            nonlocal left
+            while inflight and (block or inflight[0][0].query()):
+                ev, finishing = inflight.popleft()
+                ev.synchronize()
+                t = t_start.elapsed_time(ev) / 1e3
+                for r in finishing:
+                    r.done = t
+                    left -= 1
+                    self.mem_used -= self._bytes(r)
+                    if not self.keep:
+                        r.out = r.spins = None
+                    r.draws = None
+                block = False
+
+        while left > 0:
+            now = time.perf_counter() - wall0
+            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
+                pending.append(reqs[nxt])
+                nxt += 1
+            retire(False)
+            if len(inflight) >= self.max_inflight:
+                retire(True)
+                continue
+            fills, sweeps, finishing = [], [], []
+            taken = set()
+            for r in running:                  # next half-sweep of each running Ising run
+                c = self.clients[r.client]
+                taken.add(r.client)
+                fills.append({"st": c.handle, "d_out": r.draws,
+                              "n_per_stream": r.L * r.L // (2 * self.n_streams)})
+                sweeps.append({"d_spins": r.spins, "d_draws": r.draws, "L": r.L,
+                               "colour": r.half_done % 2, "shift": SHIFT[c.gen],
+                               "t4": self.t4, "t8": self.t8})
+                r.half_done += 1
+                r.numbers += r.L * r.L // 2
+                if r.half_done == 2 * r.sweeps:
+                    finishing.append(r)
+            keep = collections.deque()
+            active = len(running) + sum(len(f) for _, f in inflight)
+            while pending:                      # admission in arrival order
+                r = pending.popleft()
+                c = self.clients[r.client]
+                need = self._bytes(r)
+                if self.max_active and active >= self.max_active:
+                    keep.append(r)
+                    continue
+                active += 1
+                if r.client in taken or c.busy is not None or self.mem_used + need > self.mem_cap:
+                    keep.append(r)
+                    taken.add(r.client)         # a client's later requests wait behind this one
+                    continue
+                taken.add(r.client)
+                self.mem_used += need
+                with torch.cuda.stream(self.stream):
+                    if r.kind == "fill":
+                        per, total = self._fill_shape(r.n)
+                        r.out = torch.empty(total, dtype=torch.float32 if r.f32 else torch.int32,
+                                            device="cuda")
+                        fills.append({"st": c.handle, "d_out": r.out, "n_per_stream": per,
+                                      "n_valid": r.n, "f32": r.f32})
+                        r.numbers = r.n
+                        finishing.append(r)
+                    else:
+                        r.spins = torch.ones((r.L, r.L), dtype=torch.int8, device="cuda")
+                        r.draws = torch.empty(r.L * r.L // 2, dtype=torch.int32, device="cuda")
+                        c.busy = r
+                        fills.append({"st": c.handle, "d_out": r.draws,
+                                      "n_per_stream": r.L * r.L // (2 * self.n_streams)})
+                        sweeps.append({"d_spins": r.spins, "d_draws": r.draws, "L": r.L,
+                                       "colour": 0, "shift": SHIFT[c.gen],
+                                       "t4": self.t4, "t8": self.t8})
+                        r.half_done = 1
+                        r.numbers = r.L * r.L // 2
+                        running.append(r)
+            pending = keep
+            if not fills:                       # nothing to launch now
+                future = realtime and nxt < len(reqs)
+                if inflight and not future:
+                    retire(True)                # only completions can free slots or memory
+                elif future:
+                    wait = reqs[nxt].arrival - (time.perf_counter() - wall0)
+                    if wait > 0:
+                        time.sleep(min(wait, 5e-5 if inflight else 1e-3))
+                elif not inflight and pending:
+                    raise RuntimeError("a request does not fit the memory cap")
+                continue
+            sid = self.stream.cuda_stream
+            prng_batcher_launch(self.batcher, fills, sid)
+            if sweeps:
+                prng_ising_half_sweep(sweeps, sid)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.stream)
+            inflight.append((ev, finishing))
+            for r in finishing:
+                if r.kind == "ising":
+                    self.clients[r.client].busy = None
+            running = [r for r in running if r.half_done < 2 * r.sweeps]
+        self.stream.synchronize()
+        return reqs
+
+
+def latency_stats(reqs):
+    lat = sorted(r.done - r.arrival for r in reqs)
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    numbers = sum(r.numbers for r in reqs)
+    return {"requests": len(reqs), "p50_ms": 1e3 * pct(0.50), "p99_ms": 1e3 * pct(0.99),
+            "max_ms": 1e3 * lat[-1], "numbers": numbers,
+            "numbers_per_s": numbers / span if span > 0 else None, "span_s": span}

@@ -57,6 +57,54 @@ def batched_requests(n_requests: int = 20000, seed: int = 0xB47C, min_len: int =
     return out
 
 
+SERVE_CLIENTS = 512
+SERVE_STREAMS = 1024          # divides L*L/2 for every Ising size below
+SERVE_ISING_L = (256, 1024, 4096)
+SERVE_SWEEPS = 16
+SERVE_MEM_CAP = 40e9
+
+
+def serving_clients(n_clients: int = SERVE_CLIENTS, seed: int = 0x5E5E):
+    """(generator, luxury, base seed) per client: half RANLUX p = 223, the
+    rest uniform over the other five.  Client c's streams are seeded from
+    base seed seed + c * 2^32."""
+    rng = np.random.default_rng(seed)
+    others = [g for g in GENS if g != "ranlux"]
+    out = []
+    for c in range(n_clients):
+        if c % 2 == 0:
+            g, lux = "ranlux", 223
+        else:
+            g, lux = others[int(rng.integers(0, len(others)))], 0
+        out.append((g, lux, seed + (c << 32)))
+    return out
+
+
+def serving_requests(n_requests: int, rate: float, n_clients: int = SERVE_CLIENTS,
+                     seed: int = 0xA771, fill_min: int = 10**3, fill_max: int = 10**6,
+                     ising_sizes=SERVE_ISING_L, sweeps: int = SERVE_SWEEPS):
+    """Poisson arrivals at `rate` per second; each request goes to a client
+    uniformly at random and is a fill (log-uniform length in [fill_min,
+    fill_max], dtype at random) or an Ising run (L uniform over
+    ising_sizes) with probability 1/2 each.  Returns dicts."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    clients = rng.integers(0, n_clients, size=n_requests)
+    kinds = rng.integers(0, 2, size=n_requests)
+    lens = np.floor(10.0 ** rng.uniform(np.log10(fill_min), np.log10(fill_max), size=n_requests))
+    f32 = rng.integers(0, 2, size=n_requests)
+    sizes = rng.integers(0, len(ising_sizes), size=n_requests)
+    out = []
+    for i in range(n_requests):
+        if kinds[i] == 0:
+            out.append({"rid": i, "client": int(clients[i]), "kind": "fill", "arrival": float(t[i]),
+                        "n": int(lens[i]), "f32": bool(f32[i])})
+        else:
+            out.append({"rid": i, "client": int(clients[i]), "kind": "ising", "arrival": float(t[i]),
+                        "L": int(ising_sizes[int(sizes[i])]), "sweeps": sweeps})
+    return out
+
+
 def sample_rows(n_rows: int, k: int, seed: int = 1234) -> np.ndarray:
     """k distinct sorted rows, always including the first and the last."""
     rng = np.random.default_rng(seed)
