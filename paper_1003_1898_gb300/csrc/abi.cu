@@ -92,7 +92,7 @@ bool tile_supported(int gen, Tile t) {
   static const Tile simple[] = {{128, 32, 1}, {128, 32, 2}, {128, 64, 1}, {256, 32, 1}};
   static const Tile mlcg[] = {{128, 128, 1}, {256, 128, 1}};
   static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1}};
-  static const Tile mar[] = {{64, 97, 1}, {128, 97, 1}};
+  static const Tile mar[] = {{128, 128, 1}, {256, 128, 1}};
   static const Tile mt[] = {{64, 624, 1}, {128, 624, 1}, {256, 624, 1}};
   const Tile* list = simple;
   int n = 4;
@@ -111,7 +111,7 @@ int lux_index(int p) {
 }
 
 // Per generator (RANLUX: per p) launch tiles; slot 5 + i is RANLUX level i.
-Tile g_tiles[10] = {{128, 128, 1}, {128, 32, 1}, {128, 128, 1}, {128, 97, 1}, {128, 48, 1},
+Tile g_tiles[10] = {{128, 128, 1}, {128, 32, 1}, {128, 128, 1}, {256, 128, 1}, {128, 48, 1},
                     {128, 624, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}};
 
 int tile_slot(int gen, int p) {

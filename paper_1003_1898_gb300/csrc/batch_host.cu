@@ -81,6 +81,7 @@ uint32_t rows_per_item(int fam, Tile t) {
     case FAM_SEED: return 256;
     case FAM_MLCG: return 4;
     case FAM_MT: return 2;
+    case FAM_RANMAR: return (uint32_t)t.threads / 32;  // a warp per stream
     default: return (uint32_t)t.threads;
   }
 }

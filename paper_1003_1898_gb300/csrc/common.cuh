@@ -235,4 +235,104 @@ struct ColFlusher {
   }
 };
 
+// Row-major staging tile: thread t's staged draws in row t (SPW words per
+// row, SPW = 4 mod 8 so that eight threads storing the same 16-byte chunk
+// of their rows hit eight different bank quads).  RowFlusher writes tile
+// columns [0, w) of rows row0 + t to out columns g0 .. g0 + w - 1.  Lanes
+// take (row ro of a 4-row group, 16-byte chunk qq of an 8-chunk group) of
+// the output, aligned to global multiples of 4 columns: when g0 is not a
+// multiple of 4 a chunk straddles two tile chunks and is assembled from two
+// 16-byte shared loads.  Eight lanes of a row read 128 contiguous bytes of
+// shared memory, and a warp store covers 4 rows x 128 bytes of the output.
+// LIMITED: honour FillDesc::limit (batched requests).
+template <int T, int SPW, bool LIMITED = false>
+struct RowFlusher {
+  static_assert(SPW % 8 == 4, "row pitch must be 4 mod 8 words");
+  static constexpr int NW = T / 32, RIT = T / (4 * NW);
+  uint32_t* gp;        // this lane's first row, column 0
+  uint64_t rowstep;    // elements between this lane's rows
+  const uint32_t* sp;  // tile row of this lane's first row
+  int nrow, kcut, qq;
+  uint64_t ccut;
+  bool vec_ok;
+
+  __device__ __forceinline__ void init(const uint32_t* s, uint32_t* out, uint64_t pitch,
+                                       uint64_t row0, uint64_t n_rows, uint64_t limit) {
+    // A quarter-warp (one 16-byte shared access phase) reads eight chunks of
+    // one row: bank quads r * SPW / 4 + chunk (mod 8), all different.
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int r = wi * 4 + (lane >> 3);
+    qq = lane & 7;
+    rowstep = (uint64_t)NW * 4 * pitch;
+    gp = out + (row0 + r) * pitch;
+    sp = s + r * SPW;
+    uint64_t rows = n_rows;
+    if (LIMITED && pitch > 0 && (limit + pitch - 1) / pitch < rows) rows = (limit + pitch - 1) / pitch;
+    const uint64_t left = rows > row0 + r ? rows - (row0 + r) : 0;
+    const uint64_t nr = (left + (NW * 4 - 1)) / (NW * 4);
+    nrow = nr < (uint64_t)RIT ? (int)nr : RIT;
+    kcut = RIT;
+    ccut = 0;
+    if (LIMITED && pitch > 0 && limit < rows * pitch) {
+      const uint64_t last = rows - 1;
+      if (last >= row0 + r && (last - (row0 + r)) % (NW * 4) == 0) {
+        kcut = (int)((last - (row0 + r)) / (NW * 4));
+        ccut = limit - last * pitch;
+      }
+    }
+    vec_ok = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  }
+
+  template <int A>
+  __device__ __forceinline__ void flush_a(uint64_t g0, int w) const {
+    const uint64_t q0 = g0 >> 2;
+    const int nq = (int)(((g0 + (uint64_t)w + 3) >> 2) - q0);
+    for (int qb = 0; qb < nq; qb += 8) {
+      const int qi = qb + qq;
+      if (qi >= nq) continue;
+      const uint64_t gc = (q0 + qi) * 4;
+      const int c = (int)(gc - g0);           // tile column of the chunk's first element
+      uint32_t* g = gp + gc;
+      const bool full = vec_ok && c >= 0 && c + 4 <= w;
+      const uint32_t* t = sp + (c - A);       // 16-byte aligned: c = A (mod 4)
+#pragma unroll
+      for (int k = 0; k < RIT; k++) {
+        if (k >= nrow) break;
+        const uint32_t* tk = t + k * NW * 4 * SPW;
+        uint32_t v[4];
+        if (full) {
+          const uint4 lo = *reinterpret_cast<const uint4*>(tk);
+          if constexpr (A == 0) {
+            v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+          } else {
+            const uint4 hi = *reinterpret_cast<const uint4*>(tk + 4);
+            const uint32_t u[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) v[i] = u[A + i];
+          }
+          if (!LIMITED || k != kcut || gc + 4 <= ccut) {
+            st_out4(g + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
+            continue;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const int ci = c + i;
+          if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
+            st_out(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci]);
+        }
+      }
+    }
+  }
+
+  __device__ __forceinline__ void flush(uint64_t g0, int w) const {
+    switch ((uint32_t)(0u - (uint32_t)g0) & 3u) {
+      case 0: flush_a<0>(g0, w); break;
+      case 1: flush_a<1>(g0, w); break;
+      case 2: flush_a<2>(g0, w); break;
+      default: flush_a<3>(g0, w); break;
+    }
+  }
+};
+
 }  // namespace prng

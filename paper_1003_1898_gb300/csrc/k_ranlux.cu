@@ -15,9 +15,9 @@
 // dozen steps per call), and the registers are loaded from / stored to that
 // copy with the matching rotation.
 //
-// Delivered draws are staged in a column-major shared tile (see ColFlusher)
-// and written out 16 bytes at a time, so the stream-major HBM writes are
-// contiguous runs of each row.
+// Delivered draws are staged in a row-major shared tile with 16-byte stores
+// and written out 16 bytes at a time (RowFlusher), so the stream-major HBM
+// writes are contiguous runs of each row.
 #include "batch.cuh"
 
 namespace prng {
@@ -115,39 +115,39 @@ __device__ __forceinline__ void discard_cycle(uint32_t (&R)[24], uint32_t& c) {
   if constexpr (RR != 0) rotate_fixed(R, RR);
 }
 
-// `cnt` SWB steps on a ring held in shared memory (ring[j * SP], phase
-// `ph`), emitting each new word to out_col[k * SP] when emit is set.
-template <int SP, bool F32>
+// `cnt` SWB steps on a ring held in shared memory (ring[j], phase `ph`),
+// emitting each new word to out[k] when emit is set.
+template <bool F32>
 __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int cnt,
-                                        uint32_t* out_col, bool emit) {
+                                        uint32_t* out, bool emit) {
   for (int k = 0; k < cnt; k++) {
     const int i14 = ph + 14 < 24 ? ph + 14 : ph - 10;
-    const int32_t t = (int32_t)ring[i14 * SP] - (int32_t)ring[ph * SP] - (int32_t)c;
+    const int32_t t = (int32_t)ring[i14] - (int32_t)ring[ph] - (int32_t)c;
     c = (uint32_t)t >> 31;
     const uint32_t x = (uint32_t)t & 0xFFFFFFu;
-    ring[ph * SP] = x;
-    if (emit) out_col[k * SP] = lux_conv<F32>(x);
+    ring[ph] = x;
+    if (emit) out[k] = lux_conv<F32>(x);
     ph = ph + 1 < 24 ? ph + 1 : 0;
   }
   return ph;
 }
 
-// Streams [row0, row0 + T) of a fill, one per thread; smem holds KT
-// columns of T + 1 words.
+// Streams [row0, row0 + T) of a fill, one per thread; smem holds a
+// row-major tile of T rows x SPW words (KT staged columns each).
 template <int T, int KT, int P, bool F32, bool LIMITED>
 __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
-  static_assert(KT >= 48, "the tile must hold a partial block next to the 24-word scratch ring");
-  constexpr int SP = T + 1;
+  static_assert(KT == 48, "the tile holds two blocks; its second half doubles as the scratch ring");
+  constexpr int SPW = KT + 4;
   const int tid = threadIdx.x;
   const uint64_t row = row0 + tid;
   const bool active = row < d.n_rows;
   const uint64_t nr = d.n_rows;
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  ColFlusher<T, LIMITED> fl;
+  RowFlusher<T, SPW, LIMITED> fl;
   fl.init(smem, out, d.pitch, row0, nr, d.limit);
-  uint32_t* col = smem + tid;                 // this thread's row of the tile (stride SP)
-  uint32_t* ring = smem + 24 * SP + tid;      // scratch ring in tile columns 24..47
+  uint32_t* my = smem + tid * SPW;            // this thread's tile row
+  uint32_t* ring = my + 24;                   // scratch ring in columns 24..47
 
   const uint64_t n = d.n_per;
   const int pos0 = (int)d.pos;
@@ -167,17 +167,16 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   if (pos0 < 24) {
     // Finish the block a previous call left open: h draws on the shared copy.
     const int h = (int)((uint64_t)(24 - pos0) < n ? (uint64_t)(24 - pos0) : n);
-#pragma unroll
-    for (int jj = 0; jj < 24; jj++) ring[jj * SP] = active ? d.state[jj * nr + row] : 0u;
+    for (int jj = 0; jj < 24; jj++) ring[jj] = active ? d.state[jj * nr + row] : 0u;
     c = active ? d.state[24 * nr + row] : 0u;
-    const int ph = swb_smem<SP, F32>(ring, 0, c, h, col, store);
+    const int ph = swb_smem<F32>(ring, 0, c, h, my, store);
     fill = h;
     j = h;
     if (j == n) {  // the fill ends inside the open block
       if (active) {
         for (int jj = 0; jj < 24; jj++) {
           const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
-          d.state[(uint64_t)jj * nr + row] = ring[src * SP];
+          d.state[(uint64_t)jj * nr + row] = ring[src];
         }
         d.state[24 * nr + row] = c;
       }
@@ -185,22 +184,26 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
       return;
     }
 #pragma unroll
-    for (int jj = 0; jj < 24; jj++) R[jj] = ring[((jj + h) % 24) * SP] << 8;  // h == 24 - pos0 here
+    for (int jj = 0; jj < 24; jj++) R[jj] = ring[(jj + h) % 24] << 8;  // h == 24 - pos0 here
+    flush();  // the head alone, so whole blocks start at tile column 0
   } else {
 #pragma unroll
     for (int jj = 0; jj < 24; jj++) R[jj] = active ? d.state[jj * nr + row] << 8 : 0u;
     c = active ? d.state[24 * nr + row] : 0u;
   }
 
-  // Whole blocks: discard p - 24, deliver 24, all in registers.
+  // Whole blocks: discard p - 24, deliver 24, all in registers; each block
+  // is six 16-byte shared stores at tile column 0 or 24.
   while (n - j >= 24) {
     discard_cycle<P>(R, c);
     if (fill + 24 > KT) flush();
-    uint32_t* dst = col + fill * SP;
     swb24(R, c);
     if (store) {
+      uint4* dst = reinterpret_cast<uint4*>(my + fill);
 #pragma unroll
-      for (int k = 0; k < 24; k++) dst[k * SP] = lux_out<F32>(R[k]);
+      for (int q = 0; q < 6; q++)
+        dst[q] = make_uint4(lux_out<F32>(R[4 * q]), lux_out<F32>(R[4 * q + 1]),
+                            lux_out<F32>(R[4 * q + 2]), lux_out<F32>(R[4 * q + 3]));
     }
     fill += 24;
     j += 24;
@@ -212,13 +215,13 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
     discard_cycle<P>(R, c);
     if (fill > 0) flush();
 #pragma unroll
-    for (int jj = 0; jj < 24; jj++) ring[jj * SP] = R[jj] >> 8;
-    const int ph = swb_smem<SP, F32>(ring, 0, c, m, col, store);
+    for (int jj = 0; jj < 24; jj++) ring[jj] = R[jj] >> 8;
+    const int ph = swb_smem<F32>(ring, 0, c, m, my, store);
     fill = m;
     if (active) {
       for (int jj = 0; jj < 24; jj++) {
         const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
-        d.state[(uint64_t)jj * nr + row] = ring[src * SP];
+        d.state[(uint64_t)jj * nr + row] = ring[src];
       }
       d.state[24 * nr + row] = c;
     }
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
 
 // Batched RANLUX fills of luxury P: a block pops an item (T streams).
 template <int T, int KT, int P, bool F32>
-__global__ void __launch_bounds__(T, 896 / T) k_batch_ranlux(const BatchQueue q) {
+__global__ void __launch_bounds__(T, 768 / T) k_batch_ranlux(const BatchQueue q) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t slot;
   for (;;) {
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(T, 896 / T) k_batch_ranlux(const BatchQueue q)
 
 template <int T, int KT, int P, bool F32>
 static cudaError_t launch_bl(const BatchQueue& q, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)KT * (T + 1) * sizeof(uint32_t);
+  constexpr size_t bytes = (size_t)T * (KT + 4) * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_batch_ranlux<T, KT, P, F32>,
@@ -291,7 +294,7 @@ cudaError_t launch_batch_ranlux(const BatchQueue& q, int p, Tile t, bool f32, cu
 
 template <int T, int KT, int P, bool F32>
 static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)KT * (T + 1) * sizeof(uint32_t);
+  constexpr size_t bytes = (size_t)T * (KT + 4) * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_fill_ranlux<T, KT, P, F32>,

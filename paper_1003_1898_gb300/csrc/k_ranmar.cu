@@ -1,43 +1,21 @@
 // k_ranmar.cu -- RANMAR fill and skip (Section 3.5; Appendix A, "RANMAR").
 //
-// One thread per stream with the whole 97-entry lag table in registers.
-// The two table indices (i97, j97) fall together by one per draw and are
-// the same for every stream, so the state is kept in canonical order
-// (V[0] = the entry overwritten next) and the kernel walks the table 97
-// draws at a time with compile-time phase: entry k of the unrolled block
-// reads registers k and (k + 64) mod 97 and writes register k.  A fill of n
-// draws runs n / 97 full blocks and one guarded partial block; the final
-// phase is folded into the store-back addresses, so no register is ever
-// indexed at run time.  The Weyl term C_n = C_{n-1} - D mod M is evaluated
-// per draw as an offset of the block's entry value by a compile-time
-// constant, so no draw waits on the previous one.  Each block's 97 draws are staged in a column-major shared
-// tile and written out 16 bytes at a time (ColFlusher).
+// One warp per stream.  The two table indices (i97, j97) fall together by
+// one per draw and are the same for every stream, so the state is kept in
+// canonical order (V[0] = the entry overwritten next, V[k] = x_{n-97+k}
+// before draw n) and the lagged part is x_n = x_{n-97} - x_{n-33} mod 2^24.
+// Both lags exceed a warp's width, so a warp computes 32 consecutive draws
+// per step, one per lane, from a 128-slot ring of the stream's recent lag
+// values in shared memory, and writes them as one coalesced 128-byte run of
+// the stream's output row.  The Weyl term C_n = C_{n-1} - D mod M is
+// evaluated per draw as an offset of the step group's entry value by a
+// per-lane constant, so no draw waits on the previous one.
 #include "batch.cuh"
 
 namespace prng {
 
 constexpr uint32_t kRanmarD = 7654321u;    // Section 3.5: RM_CD * 2^24
 constexpr uint32_t kRanmarM = 16777213u;   // Section 3.5: RM_CM * 2^24
-
-// (k D) mod M, D = 7654321, M = 2^24 - 3 (a compile-time constant for the
-// unrolled steps).
-__host__ __device__ constexpr uint32_t ranmar_kd(int k) {
-  return (uint32_t)(((uint64_t)k * kRanmarD) % kRanmarM);
-}
-
-// Draw k (compile-time, 0-based) of a block whose Weyl term entered the
-// block as C0.  Y = V[0] - V[64] replaces V[0] (kept modulo 2^32; only its
-// low 24 bits matter).  The Weyl term after k+1 steps is C0 - (k+1) D mod M,
-// so each draw's C is an offset by a constant, independent of the previous
-// draw: with c = C0 - ((k+1) D mod M), C = c when c >= 0 and c + M otherwise,
-// and since M = 2^24 - 3, X = (Y - C) mod 2^24 = (Y - c + 3 [c < 0]) mod 2^24.
-__device__ __forceinline__ uint32_t ranmar_step(uint32_t (&R)[97], uint32_t C0, const int k) {
-  const int i0 = k % 97, i64 = (k + 64) % 97;
-  const uint32_t y = R[i0] - R[i64];
-  R[i0] = y;
-  const int32_t c = (int32_t)C0 - (int32_t)ranmar_kd(k + 1);
-  return (y - (uint32_t)c + 3u * ((uint32_t)c >> 31)) & 0xFFFFFFu;
-}
 
 // C0 after `steps` more draws.
 __device__ __forceinline__ uint32_t ranmar_advance_c(uint32_t C0, uint32_t steps) {
@@ -52,133 +30,153 @@ __device__ __forceinline__ uint32_t rm_conv(uint32_t x) {
   else return x;
 }
 
-// Streams [row0, row0 + T) of a fill, one per thread; smem holds one
-// column-major tile of 97 columns (see ColFlusher).
-template <int T, bool F32, bool LIMITED>
-__device__ __forceinline__ void ranmar_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
-  constexpr int SP = T + 1;
-  const int tid = threadIdx.x;
-  const uint64_t row = row0 + tid;
-  const bool active = row < d.n_rows;
+// Ring slots per stream: 128 for the lag table, slot 128 for C, padding to
+// 132 words so that the cooperative state load (eight streams side by side)
+// hits 32 different banks.
+constexpr int kRanmarRing = 132;
+
+// One pass over `rows` <= NW streams [row0, row0 + rows), one warp each.
+//
+// The lags (97, 33) both exceed 32, so the 32 draws x_n .. x_{n+31} depend
+// only on earlier draws: lane l computes x_{n+l}, and a warp advances its
+// stream 32 draws per step.  The stream's last 128 lag values sit in a
+// shared ring, x_m in slot (m + 97) mod 128, so the canonical table V[k] =
+// x_{k-97} loads to slots 0..96 unchanged; step draws x_n read slots n mod
+// 128 (lag 97) and (n + 64) mod 128 (lag 33) and write slot (n + 97) mod 128.
+// Every output store is one 128-byte run of the stream's row, with no
+// staging.  The state moves between HBM and the rings through one
+// cooperative pass of the block (eight consecutive streams per 32-byte
+// sector).
+template <int NW, bool F32, bool LIMITED>
+__device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, int rows,
+                                             uint32_t* smem) {
+  constexpr int RS = kRanmarRing;
   const uint64_t nr = d.n_rows;
-
-  uint32_t R[97];
-  uint32_t C = 0;
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < 97; j++) R[j] = d.state[j * nr + row];
-    C = d.state[97 * nr + row];
-  } else {
-#pragma unroll
-    for (int j = 0; j < 97; j++) R[j] = 0;
+  for (int e = threadIdx.x; e < 98 * NW; e += NW * 32) {
+    const int j = e / NW, w = e % NW;
+    if (w < rows) smem[w * RS + (j < 97 ? j : 128)] = d.state[(uint64_t)j * nr + row0 + w];
   }
+  __syncthreads();
 
-  uint32_t* out = static_cast<uint32_t*>(d.out);
-  const bool store = out != nullptr;
-  ColFlusher<T, LIMITED> fl;
-  fl.init(smem, out, d.pitch, row0, nr, d.limit);
-  uint32_t* col = smem + tid;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const uint64_t n = d.n_per;
-  const uint64_t nfull = n / 97;
-  const int m = (int)(n % 97);
-  uint64_t g0 = 0;
-
-  for (uint64_t b = 0; b < nfull; b++) {
+  if (w < rows) {
+    uint32_t* ring = smem + w * RS;
+    uint32_t C = ring[128];
+    uint32_t* out = static_cast<uint32_t*>(d.out);
+    const bool store = out != nullptr;
+    const uint64_t rbase = (row0 + w) * d.pitch;   // element index of the row's first draw
+    uint32_t* orow = store ? out + rbase : nullptr;
+    uint32_t kd[4];                                // ((32 s + l + 1) D) mod M
+    uint32_t* wp[4];                               // slot of this lane's draw in step s
 #pragma unroll
-    for (int k = 0; k < 97; k++) {
-      const uint32_t x = ranmar_step(R, C, k);
-      if (store) col[k * SP] = rm_conv<F32>(x);
+    for (int s = 0; s < 4; s++) {
+      kd[s] = (uint32_t)(((uint64_t)(32 * s + l + 1) * kRanmarD) % kRanmarM);
+      wp[s] = ring + ((32 * s + 97 + l) & 127);
     }
-    C = ranmar_advance_c(C, 97);
-    if (store) {
-      __syncthreads();
-      fl.flush(g0, 97);
-      __syncthreads();
-    }
-    g0 += 97;
-  }
-  if (m > 0) {
+    const uint32_t* rl = ring + l;
+    // Lane l's draw of step s: Y = x_{n-97} - x_{n-33}, kept modulo 2^32
+    // (only its low 24 bits matter).  The Weyl term after it is C = C_group
+    // - kd[s] mod M: with c = C_group - kd[s] as a 32-bit word, C = c when no
+    // wrap happened and c + M otherwise; since M = 2^24 - 3 and c >> 30 is 3
+    // exactly when it wrapped, X = (Y - C) mod 2^24 = (Y - c + (c >> 30))
+    // mod 2^24.
+    auto out_word = [&](uint32_t y, int s) {
+      const uint32_t c = C - kd[s];
+      return rm_conv<F32>((y - c + (c >> 30)) & 0xFFFFFFu);
+    };
+    uint64_t g = 0;
+    for (; g + 128 <= n; g += 128) {
 #pragma unroll
-    for (int k = 0; k < 97; k++) {
-      if (k < m) {
-        const uint32_t x = ranmar_step(R, C, k);
-        if (store) col[k * SP] = rm_conv<F32>(x);
+      for (int s = 0; s < 4; s++) {
+        const uint32_t y = rl[32 * s] - rl[32 * ((s + 2) & 3)];
+        *wp[s] = y;
+        __syncwarp();
+        if (store) {
+          const uint32_t v = out_word(y, s);
+          if (!LIMITED || rbase + g + 32 * s + l < d.limit) st_out(orow + g + 32 * s + l, v);
+        }
       }
+      C = ranmar_advance_c(C, 128);
     }
-    C = ranmar_advance_c(C, (uint32_t)m);
-    if (store) {
-      __syncthreads();
-      fl.flush(g0, m);
-    }
-  }
-
-  if (active) {
-    // After n draws the ring phase is m: canonical V[k] = R[(k + m) % 97].
+    const int rem = (int)(n - g);
+    if (rem > 0) {
 #pragma unroll
-    for (int r = 0; r < 97; r++) {
-      const int k = (r - m + 97) % 97;
-      d.state[(uint64_t)k * nr + row] = R[r] & 0xFFFFFFu;
+      for (int s = 0; s < 4; s++) {
+        if (32 * s < rem) {
+          const bool on = 32 * s + l < rem;
+          uint32_t y = 0;
+          if (on) {
+            y = rl[32 * s] - rl[32 * ((s + 2) & 3)];
+            *wp[s] = y;
+          }
+          __syncwarp();
+          if (on && store) {
+            const uint32_t v = out_word(y, s);
+            if (!LIMITED || rbase + g + 32 * s + l < d.limit) st_out(orow + g + 32 * s + l, v);
+          }
+        }
+      }
+      C = ranmar_advance_c(C, (uint32_t)rem);
     }
-    d.state[97 * nr + row] = C;
+    __syncwarp();
+    if (l == 0) ring[128] = C;
+  }
+  __syncthreads();
+
+  // Canonical order after n draws: V[k] = x_{n-97+k}, in slot (n + k) mod 128.
+  const int off = (int)(n & 127);
+  for (int e = threadIdx.x; e < 98 * NW; e += NW * 32) {
+    const int j = e / NW, w2 = e % NW;
+    if (w2 < rows) {
+      const uint32_t v = j < 97 ? smem[w2 * RS + ((off + j) & 127)] & 0xFFFFFFu : smem[w2 * RS + 128];
+      d.state[(uint64_t)j * nr + row0 + w2] = v;
+    }
   }
 }
 
 template <int T, bool F32>
-__global__ void __launch_bounds__(T, 512 / T) k_fill_ranmar(const FillDesc d) {
-  extern __shared__ uint32_t smem[];
-  ranmar_rows<T, F32, false>(d, (uint64_t)blockIdx.x * T, smem);
+__global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
+  __shared__ uint32_t smem[(T / 32) * kRanmarRing];
+  const uint64_t row0 = (uint64_t)blockIdx.x * (T / 32);
+  const uint64_t left = d.n_rows - row0;
+  ranmar_warps<T / 32, F32, false>(d, row0, left < (uint64_t)(T / 32) ? (int)left : T / 32, smem);
 }
 
-// Batched RANMAR fills: one block per item (T streams of one request),
-// items ordered longest first.  With the 97-word lag table in registers a
-// persistent loop around the body does not fit the register budget, so
-// here the hardware block scheduler hands out the items in order.
+// Batched RANMAR fills: one block per item (up to T / 32 streams of one
+// request, items ordered longest first, handed out in order by the block
+// scheduler).
 template <int T, bool F32>
-__global__ void __launch_bounds__(T, 512 / T) k_batch_ranmar(const BatchQueue q) {
-  extern __shared__ uint32_t smem[];
+__global__ void __launch_bounds__(T) k_batch_ranmar(const BatchQueue q) {
+  __shared__ uint32_t smem[(T / 32) * kRanmarRing];
   const BatchItem si = q.items[blockIdx.x];
-  ranmar_rows<T, F32, true>(q.reqs[si.req].d, si.row0, smem);
+  ranmar_warps<T / 32, F32, true>(q.reqs[si.req].d, si.row0, (int)si.rows, smem);
 }
 
 template <int T, bool F32>
 static cudaError_t launch_bm(const BatchQueue& q, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)97 * (T + 1) * sizeof(uint32_t);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_ranmar<T, F32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  k_batch_ranmar<T, F32><<<q.n_items, T, bytes, s>>>(q);
+  k_batch_ranmar<T, F32><<<q.n_items, T, 0, s>>>(q);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_ranmar(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
   if (q.n_items == 0) return cudaSuccess;
   if (t.threads == 128) return f32 ? launch_bm<128, true>(q, s) : launch_bm<128, false>(q, s);
-  return f32 ? launch_bm<64, true>(q, s) : launch_bm<64, false>(q, s);
+  return f32 ? launch_bm<256, true>(q, s) : launch_bm<256, false>(q, s);
 }
 
 template <int T, bool F32>
 static cudaError_t launch_m(const FillDesc& d, cudaStream_t s) {
-  constexpr size_t bytes = (size_t)97 * (T + 1) * sizeof(uint32_t);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fill_ranmar<T, F32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  const uint64_t grid = (d.n_rows + T - 1) / T;
-  k_fill_ranmar<T, F32><<<(unsigned)grid, T, d.out ? bytes : 0, s>>>(d);
+  const uint64_t grid = (d.n_rows + T / 32 - 1) / (T / 32);
+  if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  k_fill_ranmar<T, F32><<<(unsigned)grid, T, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_ranmar(const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
   if (t.threads == 128) return d.f32 ? launch_m<128, true>(d, s) : launch_m<128, false>(d, s);
-  return d.f32 ? launch_m<64, true>(d, s) : launch_m<64, false>(d, s);
+  return d.f32 ? launch_m<256, true>(d, s) : launch_m<256, false>(d, s);
 }
 
 }  // namespace prng

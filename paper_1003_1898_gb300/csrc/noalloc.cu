@@ -80,6 +80,7 @@ uint32_t rows_per_item(int fam) {
     case FAM_SEED: return 256;
     case FAM_MLCG: return 4;
     case FAM_MT: return 2;
+    case FAM_RANMAR: return (uint32_t)tile_of(fam).threads / 32;  // a warp per stream
     default: return (uint32_t)tile_of(fam).threads;
   }
 }

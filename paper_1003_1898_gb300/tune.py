@@ -26,7 +26,7 @@ TILES = {
     "ggl": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
     "ranecu": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
     "ranlux": [(64, 48, 1), (128, 48, 1), (256, 48, 1)],
-    "ranmar": [(64, 97, 1), (128, 97, 1)],
+    "ranmar": [(128, 128, 1), (256, 128, 1)],
     "mt19937": [(64, 624, 1), (128, 624, 1), (256, 624, 1)],
 }
 
