@@ -4,10 +4,10 @@
 // One thread per stream.  In the hot loop the 24-word RCARRY ring and the
 // borrow live in registers and the ring is walked 24 steps at a time with a
 // compile-time phase, so both lags (x_{n-10}, x_{n-24}) are fixed registers
-// and no register is indexed at run time; eight steps at a time run as one
-// subtract-with-borrow chain (swb8).  A luxury cycle is 24 delivered
-// steps plus p - 24 discarded ones; p - 24 = 24 q + r runs as q unrolled
-// 24-step groups, r single steps and one fixed register permutation.
+// and no register is indexed at run time; 24 steps at a time run as one
+// subtract-with-borrow chain (swb24).  A luxury cycle is 24 delivered
+// steps plus p - 24 discarded ones; p - 24 = 24 q + r runs as q 24-step
+// chains, one r-step chain and one fixed register permutation.
 //
 // The pieces whose length is only known at run time -- the head of a fill
 // that resumes inside a block and the tail of a fill that stops inside one --
@@ -39,46 +39,102 @@ __device__ __forceinline__ void swb_step(uint32_t (&R)[24], uint32_t& c, const i
   R[i0] = t & 0xFFFFFF00u;
 }
 
-// Steps K0 .. K0+7 as one chain of subtract-with-borrow instructions; the
-// borrow travels in the carry flag, so the serial dependence per step is a
-// single instruction.  The lags (k + 14) % 24 of these steps never fall in
-// [K0, K0 + 8), so they are plain inputs.
-template <int K0>
-__device__ __forceinline__ void swb8(uint32_t (&R)[24], uint32_t& c) {
+// One SWB step of a carry chain on asm operands k (the word replaced) and
+// l (its lag-10 partner): X_k = X_l - X_k - borrow, low byte cleared.
+#define LUX_SWB(k, l) "subc.cc.u32 %" k ", %" l ", %" k ";\n\tand.b32 %" k ", %" k ", -256;\n\t"
+
+// 24 steps from phase 0 as one subtract-with-borrow chain: the borrow
+// travels in the carry flag, so the serial dependence per step is a single
+// instruction, and it enters and leaves the flag once per 24 steps.  Step k
+// replaces word k with word (k + 14) % 24 minus word k; for k >= 10 that
+// partner was already replaced earlier in the chain, as the recurrence
+// requires.  The ring returns to phase 0.
+__device__ __forceinline__ void swb24(uint32_t (&R)[24], uint32_t& c) {
   asm("{\n\t"
       ".reg .u32 t;\n\t"
-      "sub.cc.u32 t, 0, %8;\n\t"
-      "subc.cc.u32 %0, %9, %0;\n\t"
-      "and.b32 %0, %0, -256;\n\t"
-      "subc.cc.u32 %1, %10, %1;\n\t"
-      "and.b32 %1, %1, -256;\n\t"
-      "subc.cc.u32 %2, %11, %2;\n\t"
-      "and.b32 %2, %2, -256;\n\t"
-      "subc.cc.u32 %3, %12, %3;\n\t"
-      "and.b32 %3, %3, -256;\n\t"
-      "subc.cc.u32 %4, %13, %4;\n\t"
-      "and.b32 %4, %4, -256;\n\t"
-      "subc.cc.u32 %5, %14, %5;\n\t"
-      "and.b32 %5, %5, -256;\n\t"
-      "subc.cc.u32 %6, %15, %6;\n\t"
-      "and.b32 %6, %6, -256;\n\t"
-      "subc.cc.u32 %7, %16, %7;\n\t"
-      "and.b32 %7, %7, -256;\n\t"
-      "subc.u32 %8, 0, 0;\n\t"
-      "and.b32 %8, %8, 1;\n\t"
+      "sub.cc.u32 t, 0, %24;\n\t"
+      LUX_SWB("0", "14")
+      LUX_SWB("1", "15")
+      LUX_SWB("2", "16")
+      LUX_SWB("3", "17")
+      LUX_SWB("4", "18")
+      LUX_SWB("5", "19")
+      LUX_SWB("6", "20")
+      LUX_SWB("7", "21")
+      LUX_SWB("8", "22")
+      LUX_SWB("9", "23")
+      LUX_SWB("10", "0")
+      LUX_SWB("11", "1")
+      LUX_SWB("12", "2")
+      LUX_SWB("13", "3")
+      LUX_SWB("14", "4")
+      LUX_SWB("15", "5")
+      LUX_SWB("16", "6")
+      LUX_SWB("17", "7")
+      LUX_SWB("18", "8")
+      LUX_SWB("19", "9")
+      LUX_SWB("20", "10")
+      LUX_SWB("21", "11")
+      LUX_SWB("22", "12")
+      LUX_SWB("23", "13")
+      "subc.u32 %24, 0, 0;\n\t"
+      "and.b32 %24, %24, 1;\n\t"
       "}"
-      : "+r"(R[K0]), "+r"(R[K0 + 1]), "+r"(R[K0 + 2]), "+r"(R[K0 + 3]), "+r"(R[K0 + 4]),
-        "+r"(R[K0 + 5]), "+r"(R[K0 + 6]), "+r"(R[K0 + 7]), "+r"(c)
-      : "r"(R[(K0 + 14) % 24]), "r"(R[(K0 + 15) % 24]), "r"(R[(K0 + 16) % 24]),
-        "r"(R[(K0 + 17) % 24]), "r"(R[(K0 + 18) % 24]), "r"(R[(K0 + 19) % 24]),
-        "r"(R[(K0 + 20) % 24]), "r"(R[(K0 + 21) % 24]));
+      : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]),
+        "+r"(R[7]), "+r"(R[8]), "+r"(R[9]), "+r"(R[10]), "+r"(R[11]), "+r"(R[12]), "+r"(R[13]),
+        "+r"(R[14]), "+r"(R[15]), "+r"(R[16]), "+r"(R[17]), "+r"(R[18]), "+r"(R[19]),
+        "+r"(R[20]), "+r"(R[21]), "+r"(R[22]), "+r"(R[23]), "+r"(c));
 }
 
-// 24 steps from phase 0 (the ring returns to phase 0).
-__device__ __forceinline__ void swb24(uint32_t (&R)[24], uint32_t& c) {
-  swb8<0>(R, c);
-  swb8<8>(R, c);
-  swb8<16>(R, c);
+// The first N steps from phase 0 (N <= 10, so every partner, word 14 + k,
+// is still unreplaced) as one chain; lengths without a chain fall back to
+// single steps.
+template <int N>
+__device__ __forceinline__ void swb_head(uint32_t (&R)[24], uint32_t& c) {
+  if constexpr (N == 1) {
+    asm("{\n\t"
+        ".reg .u32 t;\n\t"
+        "sub.cc.u32 t, 0, %1;\n\t"
+        LUX_SWB("0", "2")
+        "subc.u32 %1, 0, 0;\n\t"
+        "and.b32 %1, %1, 1;\n\t"
+        "}"
+        : "+r"(R[0]), "+r"(c)
+        : "r"(R[14]));
+  } else if constexpr (N == 5) {
+    asm("{\n\t"
+        ".reg .u32 t;\n\t"
+        "sub.cc.u32 t, 0, %5;\n\t"
+        LUX_SWB("0", "6")
+        LUX_SWB("1", "7")
+        LUX_SWB("2", "8")
+        LUX_SWB("3", "9")
+        LUX_SWB("4", "10")
+        "subc.u32 %5, 0, 0;\n\t"
+        "and.b32 %5, %5, 1;\n\t"
+        "}"
+        : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(c)
+        : "r"(R[14]), "r"(R[15]), "r"(R[16]), "r"(R[17]), "r"(R[18]));
+  } else if constexpr (N == 7) {
+    asm("{\n\t"
+        ".reg .u32 t;\n\t"
+        "sub.cc.u32 t, 0, %7;\n\t"
+        LUX_SWB("0", "8")
+        LUX_SWB("1", "9")
+        LUX_SWB("2", "10")
+        LUX_SWB("3", "11")
+        LUX_SWB("4", "12")
+        LUX_SWB("5", "13")
+        LUX_SWB("6", "14")
+        "subc.u32 %7, 0, 0;\n\t"
+        "and.b32 %7, %7, 1;\n\t"
+        "}"
+        : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]), "+r"(c)
+        : "r"(R[14]), "r"(R[15]), "r"(R[16]), "r"(R[17]), "r"(R[18]), "r"(R[19]), "r"(R[20]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; k++) swb_step(R, c, k);
+  }
 }
 
 // new R[j] = R[(j + s) % 24] for a compile-time s.
@@ -110,8 +166,7 @@ __device__ __forceinline__ void discard_cycle(uint32_t (&R)[24], uint32_t& c) {
   constexpr int D = P - 24, Q = D / 24, RR = D % 24;
 #pragma unroll 1
   for (int g = 0; g < Q; g++) swb24(R, c);
-#pragma unroll
-  for (int k = 0; k < RR; k++) swb_step(R, c, k);
+  swb_head<RR>(R, c);
   if constexpr (RR != 0) rotate_fixed(R, RR);
 }
 
