@@ -195,6 +195,33 @@ def cpu_oracle_rate(sample_per_item: int):
     return n_total / t_total, t_total
 
 
+def cpu_oracle_rate_threads(sample_per_item: int, threads: int):
+    """The same mix with every item split over `threads` host threads (the
+    oracle's C functions release the GIL): thread t draws its share from its
+    own stream (jump items: its own serial sequence).  Returns numbers/s."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.lib()
+    per = max(1, sample_per_item // threads)
+    t_total = 0.0
+    n_total = 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for label, g, kind, numbers in step_items():
+            lux = RANLUX_P if g == "ranlux" else 0
+            if kind == "jump":
+                work = lambda t: oracle.serial_fill(g, JUMP_X0[g] + 2 * t, per)
+            elif kind == "f32":
+                work = lambda t: oracle.fill(g, SEED, 1, per, luxury=lux, stream0=t, want_f32=True)
+            else:
+                work = lambda t: oracle.checksum_draws(g, SEED, t, per, luxury=lux)
+            t0 = time.perf_counter()
+            list(ex.map(work, range(threads)))
+            dt = time.perf_counter() - t0
+            t_total += dt * (numbers / (per * threads))
+            n_total += numbers
+    return n_total / t_total
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -222,6 +249,50 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+
+LUX_STREAMS, LUX_PER = 65536, 4096
+INT_LANES_PER_SM = 64      # 32-bit integer ALU lanes per SM per clock (half the FP32 rate)
+
+
+def measure_luxury_sweep(P, torch, dev, stream, sm_mhz):
+    """ns/number of RANLUX f32 fills (2^28 over 65,536 streams) for every
+    standard p, and the fraction of the integer-pipe bound reached.  The
+    bound counts the subtract-with-borrow chains alone: p/24 steps per
+    delivered number, each one subtract-with-borrow plus one low-byte clear,
+    plus 3 instructions per 24-step chain to move the borrow in and out of
+    the carry flag; the pipe retires INT_LANES_PER_SM lanes per SM per clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    out = torch.empty(LUX_STREAMS * LUX_PER, dtype=torch.float32, device=dev)
+    res = {"workload": f"{LUX_STREAMS} streams x {LUX_PER} f32 per p (2^28 numbers)",
+           "sm_count": sms, "sm_mhz": mhz, "int_lanes_per_sm_clk": INT_LANES_PER_SM, "levels": {}}
+    for p in (24, 48, 97, 223, 389, 120, 240, 408):
+        h = P.prng_create("ranlux", SEED, LUX_STREAMS, p)
+        sid = stream.cuda_stream
+        for _ in range(2):
+            P.prng_fill_f32(h, out.data_ptr(), LUX_PER, sid)
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            P.prng_fill_f32(h, out.data_ptr(), LUX_PER, sid)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        P.prng_destroy(h)
+        ms = statistics.median(ts)
+        n = LUX_STREAMS * LUX_PER
+        instr = (p / 24.0) * (2.0 + 3.0 / 24.0)
+        bound_ms = 1e3 * n * instr / (sms * INT_LANES_PER_SM * mhz * 1e6)
+        hbm_ms = 1e3 * 4 * n / (peaks()[0] * 1e9)
+        res["levels"][str(p)] = {"ms": ms, "ns_per_number": 1e6 * ms / n, "numbers_per_s": n / (ms / 1e3),
+                                 "int_instr_per_number": instr, "int_bound_ms": bound_ms,
+                                 "hbm_bound_ms": hbm_ms,
+                                 "frac_of_bound": max(bound_ms, hbm_ms) / ms,
+                                 "bound": "alu" if bound_ms > hbm_ms else "hbm"}
+    del out
+    return res
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -326,6 +397,10 @@ def run_ours(args, rank, world, local_rank):
     roof["write_only_gbs"] = write_only_gbs
     roof["frac_of_write_only"] = per[dl]["gbs"] / write_only_gbs
 
+    # RANLUX luxury sweep: 2^28 f32 per p over 65,536 streams, against the
+    # integer-pipe bound of the subtract-with-borrow chains.
+    lux_sweep = measure_luxury_sweep(P, torch, dev, stream, clk.summary().get("sm_mhz"))
+
     # Batched requests (20,000 mixed fills): one graph launch vs one plain
     # re-seed + fill per request.
     batched = None
@@ -351,12 +426,17 @@ def run_ours(args, rank, world, local_rank):
         P.prng_destroy(h)
     if rank != 0:
         return
-    cpu = None
+    cpu = cpu_mt = None
     if world == 1 and not args.no_cpu:
         rate, secs = cpu_oracle_rate(args.cpu_sample)
         cpu = {"value": rate, "unit": "numbers/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_sample} draws per step item ({len(items)} items), single "
                          f"thread, weighted by the step's mix"}
+        nthr = os.cpu_count() or 1
+        rate_mt = cpu_oracle_rate_threads(args.cpu_sample, nthr)
+        cpu_mt = {"value": rate_mt, "unit": "numbers/s", "cores": nthr, "kind": "oracle",
+                  "sample": f"{args.cpu_sample} draws per step item split over {nthr} threads "
+                            f"(one stream each), weighted by the step's mix"}
     line = {
         "metric": METRIC, "value": value, "unit": "numbers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -372,7 +452,9 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_mt,
         "per_kernel": per,
+        "luxury_sweep": lux_sweep,
         "tiles": {"tuned_cache": bool(tuned),
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }

@@ -45,7 +45,7 @@ typedef enum prng_gen {
 enum {
   PRNG_OK = 0,
   PRNG_EGEN = -1,        /* unknown generator                                   */
-  PRNG_ELUXURY = -2,     /* RANLUX luxury not in {0..4, 24, 48, 97, 223, 389}    */
+  PRNG_ELUXURY = -2,     /* RANLUX luxury not in {0..4, 24, 48, 97, 223, 389, 120, 240, 408} */
   PRNG_ESIZE = -3,       /* zero streams/chunks, or a size that overflows        */
   PRNG_ENULL = -4,       /* a required pointer is NULL                           */
   PRNG_EALLOC = -5,      /* device allocation failed                             */
@@ -71,8 +71,10 @@ typedef struct prng_state prng_state;
  *   31329, kl = hi32(s) mod 30082) (Section 3.5); RANLUX table from the MLCG
  *   40014 mod 2147483563 started at s mod 2147483563 (19780503 if 0);
  *   MT19937 init_genrand(lo32(s)).
- * `luxury` selects RANLUX's p (levels 0..4 or p in {24,48,97,223,389},
- * Appendix A "RANLUX"); it is ignored for the other generators.
+ * `luxury` selects RANLUX's p: levels 0..4 or p in {24,48,97,223,389}
+ * (Appendix A "RANLUX"), or p in {120,240,408}, the planar scheme of
+ * Section 3.6 (24 numbers delivered, then 96, 216 or 384 discarded; its
+ * first level is p = 48).  It is ignored for the other generators.
  * On success *out owns device memory until prng_destroy(). */
 int prng_create(prng_state **out, prng_gen_t gen, uint64_t seed, uint32_t n_streams,
                 uint32_t luxury);

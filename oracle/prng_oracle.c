@@ -177,12 +177,17 @@ uint32_t orc_ranmar_next(orc_ranmar *s) {
 /* ---------------------------------------------------------------- RANLUX */
 
 /* Luxury level -> p (Appendix A, "RANLUX": levels 0..4 are p = 24, 48, 97,
- * 223, 389).  p itself is accepted too. */
+ * 223, 389).  p itself is accepted too, and so are the p of Section 3.6's
+ * planar scheme, which discards a multiple of 24 after each 24 delivered
+ * numbers (24, 96, 216, 384 at levels 1..4): p = 48, 120, 240, 408. */
 int32_t orc_luxury_p(int32_t luxury) {
   static const int32_t P[5] = {24, 48, 97, 223, 389};
+  static const int32_t PLANAR[3] = {120, 240, 408};
   if (luxury >= 0 && luxury <= 4) return P[luxury];
   for (int i = 0; i < 5; i++)
     if (luxury == P[i]) return luxury;
+  for (int i = 0; i < 3; i++)
+    if (luxury == PLANAR[i]) return luxury;
   return -1;
 }
 

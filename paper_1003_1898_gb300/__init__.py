@@ -18,6 +18,7 @@ GGL, XOR128, RANECU, RANMAR, RANLUX, MT19937 = range(6)
 GEN_NAMES = ("ggl", "xor128", "ranecu", "ranmar", "ranlux", "mt19937")
 GEN_IDS = {n: i for i, n in enumerate(GEN_NAMES)}
 LUXURY_P = (24, 48, 97, 223, 389)
+PLANAR_P = (48, 120, 240, 408)          # Section 3.6 planar scheme: 24, 96, 216, 384 discarded
 STATE_WORDS = (1, 4, 2, 98, 25, 624)
 
 _lib = None

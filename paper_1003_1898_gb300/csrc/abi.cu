@@ -106,13 +106,19 @@ bool tile_supported(int gen, Tile t) {
   return false;
 }
 
+// Index of a RANLUX p: the standard levels 24, 48, 97, 223, 389, then the
+// planar scheme's 120, 240, 408.
 int lux_index(int p) {
-  switch (p) { case 24: return 0; case 48: return 1; case 97: return 2; case 223: return 3; default: return 4; }
+  static const int P[8] = {24, 48, 97, 223, 389, 120, 240, 408};
+  for (int i = 0; i < 8; i++)
+    if (P[i] == p) return i;
+  return 0;
 }
 
-// Per generator (RANLUX: per p) launch tiles; slot 5 + i is RANLUX level i.
-Tile g_tiles[10] = {{128, 128, 1}, {128, 32, 1}, {128, 128, 1}, {256, 128, 1}, {128, 48, 1},
-                    {128, 624, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}};
+// Per generator (RANLUX: per p) launch tiles; slot 5 + i is RANLUX p index i >= 1.
+Tile g_tiles[13] = {{128, 128, 1}, {128, 32, 1}, {128, 128, 1}, {256, 128, 1}, {128, 48, 1},
+                    {128, 624, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1}, {128, 48, 1},
+                    {128, 48, 1}, {128, 48, 1}, {128, 48, 1}};
 
 int tile_slot(int gen, int p) {
   if (gen != RANLUX) return gen;

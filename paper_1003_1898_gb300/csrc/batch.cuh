@@ -29,12 +29,59 @@ struct BatchItem {
 
 // Families, each with its own item array and counter.  Fills are split by
 // output type as well (the float form of a family is kind + FAM_F32).
+// RANLUX has one family per luxury p (the p is a kernel template argument).
 enum BatchFamily : int {
   FAM_SEED = 0, FAM_MLCG, FAM_XOR128, FAM_RANMAR, FAM_MT,
-  FAM_LUX24, FAM_LUX48, FAM_LUX97, FAM_LUX223, FAM_LUX389, FAM_KINDS,
+  FAM_LUX24, FAM_LUX48, FAM_LUX97, FAM_LUX223, FAM_LUX389,
+  FAM_LUX120, FAM_LUX240, FAM_LUX408, FAM_KINDS,
   FAM_F32 = FAM_KINDS - 1,
   FAM_COUNT = 2 * FAM_KINDS - 1
 };
+
+// The luxury p of each RANLUX family, in family order from FAM_LUX24.
+constexpr int kLuxFamilyP[FAM_KINDS - FAM_LUX24] = {24, 48, 97, 223, 389, 120, 240, 408};
+
+inline int family_of(int gen, int p) {
+  switch (gen) {
+    case GGL:
+    case RANECU: return FAM_MLCG;
+    case XOR128: return FAM_XOR128;
+    case RANMAR: return FAM_RANMAR;
+    case MT19937: return FAM_MT;
+    default:
+      for (int i = 0; i < FAM_KINDS - FAM_LUX24; i++)
+        if (kLuxFamilyP[i] == p) return FAM_LUX24 + i;
+      return -1;
+  }
+}
+// Family of a fill (the MLCG kernel takes the output type at run time).
+inline int fill_family(int gen, int p, bool f32) {
+  const int kind = family_of(gen, p);
+  return (f32 && kind != FAM_MLCG) ? kind + FAM_F32 : kind;
+}
+inline int kind_of(int fam) { return fam >= FAM_KINDS ? fam - FAM_F32 : fam; }
+inline bool is_f32_family(int fam) { return fam >= FAM_KINDS; }
+inline int lux_p_of(int fam) { return kLuxFamilyP[kind_of(fam) - FAM_LUX24]; }
+
+// Launch tile of a family (the generator's current default tile).
+inline Tile tile_of(int fam) {
+  const int k = kind_of(fam);
+  if (k == FAM_SEED) return Tile{256, 0, 1};
+  if (k >= FAM_LUX24) return default_tile(RANLUX, lux_p_of(fam));
+  const int gen = k == FAM_MLCG ? GGL : k == FAM_XOR128 ? XOR128 : k == FAM_RANMAR ? RANMAR : MT19937;
+  return default_tile(gen, 0);
+}
+
+// Streams per work item of a family launched with tile t.
+inline uint32_t rows_per_item(int fam, Tile t) {
+  switch (kind_of(fam)) {
+    case FAM_SEED: return 256;
+    case FAM_MLCG: return 4;
+    case FAM_MT: return 2;
+    case FAM_RANMAR: return (uint32_t)t.threads / 32;  // a warp per stream
+    default: return (uint32_t)t.threads;
+  }
+}
 
 struct BatchQueue {
   const BatchReq* reqs;

@@ -49,43 +49,6 @@ struct prng_batch {
 
 namespace {
 
-int family_of(int gen, int p) {
-  switch (gen) {
-    case GGL:
-    case RANECU: return FAM_MLCG;
-    case XOR128: return FAM_XOR128;
-    case RANMAR: return FAM_RANMAR;
-    case MT19937: return FAM_MT;
-    default:
-      switch (p) {
-        case 24: return FAM_LUX24;
-        case 48: return FAM_LUX48;
-        case 97: return FAM_LUX97;
-        case 223: return FAM_LUX223;
-        default: return FAM_LUX389;
-      }
-  }
-}
-
-int kind_of(int fam) { return fam >= FAM_KINDS ? fam - FAM_F32 : fam; }
-bool is_f32(int fam) { return fam >= FAM_KINDS; }
-
-int lux_p_of(int fam) {
-  static const int P[5] = {24, 48, 97, 223, 389};
-  return P[kind_of(fam) - FAM_LUX24];
-}
-
-// Streams per work item of a family.
-uint32_t rows_per_item(int fam, Tile t) {
-  switch (kind_of(fam)) {
-    case FAM_SEED: return 256;
-    case FAM_MLCG: return 4;
-    case FAM_MT: return 2;
-    case FAM_RANMAR: return (uint32_t)t.threads / 32;  // a warp per stream
-    default: return (uint32_t)t.threads;
-  }
-}
-
 void destroy_batch(prng_batch* b) {
   if (b == nullptr) return;
   for (auto& u : b->buf) {
@@ -127,7 +90,7 @@ cudaError_t capture(prng_batch* b, Buffers& u) {
     cudaStreamWaitEvent(s, b->fork, 0);
     const BatchQueue q = queue(f);
     const Tile t = b->fam_tile[f];
-    const bool f32 = is_f32(f);
+    const bool f32 = is_f32_family(f);
     switch (kind_of(f)) {
       case FAM_MLCG: launch_batch_mlcg(q, t, s); break;
       case FAM_XOR128: launch_batch_xor128(q, t, f32, s); break;
@@ -182,11 +145,7 @@ int prng_batch_create(prng_batch** out, const prng_fill_req* reqs, uint32_t n_re
   std::vector<std::vector<BatchItem>> items(FAM_COUNT);
   std::vector<std::vector<uint64_t>> cost(FAM_COUNT);
   for (int f = 0; f < FAM_COUNT; f++) {
-    const int k = kind_of(f);
-    const int gen = k == FAM_MLCG ? GGL : k == FAM_XOR128 ? XOR128 : k == FAM_RANMAR ? RANMAR
-                  : k == FAM_MT ? MT19937 : RANLUX;
-    b->fam_tile[f] = k >= FAM_LUX24 ? default_tile(RANLUX, lux_p_of(f))
-                   : k == FAM_SEED ? Tile{256, 0, 1} : default_tile(gen, 0);
+    b->fam_tile[f] = tile_of(f);
   }
   for (uint32_t i = 0; i < n_reqs; i++) {
     const prng_fill_req& r = reqs[i];

@@ -17,10 +17,14 @@ struct prng_state {
 
 namespace prng {
 
+// Luxury level or p -> p: levels 0..4 are the standard p = 24, 48, 97, 223,
+// 389 (Appendix A, "RANLUX"); p itself is accepted, and so are the planar
+// scheme's p = 120, 240, 408 (Section 3.6: 96, 216, 384 discarded after each
+// 24 delivered; its level 1, p = 48, is standard p = 48).
 inline int luxury_to_p(uint32_t luxury) {
-  static const int P[5] = {24, 48, 97, 223, 389};
+  static const int P[8] = {24, 48, 97, 223, 389, 120, 240, 408};
   if (luxury <= 4) return P[luxury];
-  for (int i = 0; i < 5; i++)
+  for (int i = 0; i < 8; i++)
     if ((int)luxury == P[i]) return P[i];
   return -1;
 }

@@ -45,49 +45,6 @@ std::mutex g_lock;
 constexpr int kMaxDevices = 64;
 unsigned char* g_dev_ptr[kMaxDevices] = {};
 
-// Family helpers (same rules as the allocating batch planner).
-int family_of(int gen, int p) {
-  switch (gen) {
-    case GGL:
-    case RANECU: return FAM_MLCG;
-    case XOR128: return FAM_XOR128;
-    case RANMAR: return FAM_RANMAR;
-    case MT19937: return FAM_MT;
-    default:
-      switch (p) {
-        case 24: return FAM_LUX24;
-        case 48: return FAM_LUX48;
-        case 97: return FAM_LUX97;
-        case 223: return FAM_LUX223;
-        default: return FAM_LUX389;
-      }
-  }
-}
-int kind_of(int fam) { return fam >= FAM_KINDS ? fam - FAM_F32 : fam; }
-int lux_p_of(int fam) {
-  static const int P[5] = {24, 48, 97, 223, 389};
-  return P[kind_of(fam) - FAM_LUX24];
-}
-Tile tile_of(int fam) {
-  const int k = kind_of(fam);
-  if (k == FAM_SEED) return Tile{256, 0, 1};
-  if (k >= FAM_LUX24) return default_tile(RANLUX, lux_p_of(fam));
-  const int gen = k == FAM_MLCG ? GGL : k == FAM_XOR128 ? XOR128 : k == FAM_RANMAR ? RANMAR : MT19937;
-  return default_tile(gen, 0);
-}
-uint32_t rows_per_item(int fam) {
-  switch (kind_of(fam)) {
-    case FAM_SEED: return 256;
-    case FAM_MLCG: return 4;
-    case FAM_MT: return 2;
-    case FAM_RANMAR: return (uint32_t)tile_of(fam).threads / 32;  // a warp per stream
-    default: return (uint32_t)tile_of(fam).threads;
-  }
-}
-int fill_family(const prng_fill_req& r) {
-  const int kind = family_of(r.st->gen, r.st->p);
-  return (r.f32 && kind != FAM_MLCG) ? kind + FAM_F32 : kind;
-}
 
 }  // namespace
 
@@ -107,8 +64,8 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
       if (reqs[j].st == r.st) return PRNG_EBLOB;
     if (r.reseed) fam_n[FAM_SEED] += (r.st->n_streams + 255) / 256;
     if (r.n_per_stream > 0) {
-      const int f = fill_family(r);
-      const uint32_t per = rows_per_item(f);
+      const int f = fill_family(r.st->gen, r.st->p, r.f32 != 0);
+      const uint32_t per = rows_per_item(f, tile_of(f));
       fam_n[f] += (r.st->n_streams + per - 1) / per;
     }
   }
@@ -165,8 +122,8 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
         h_items[fill_at[FAM_SEED]++] =
             BatchItem{i, (uint32_t)std::min<uint64_t>(256, st->n_streams - r0), r0};
     if (r.n_per_stream > 0) {
-      const int f = fill_family(r);
-      const uint32_t per = rows_per_item(f);
+      const int f = fill_family(r.st->gen, r.st->p, r.f32 != 0);
+      const uint32_t per = rows_per_item(f, tile_of(f));
       for (uint64_t r0 = 0; r0 < st->n_streams; r0 += per)
         h_items[fill_at[f]++] =
             BatchItem{i, (uint32_t)std::min<uint64_t>(per, st->n_streams - r0), r0};

@@ -15,7 +15,7 @@ import argparse
 import json
 import os
 
-from . import GEN_NAMES, LUXURY_P, prng_create, prng_destroy, prng_fill_f32, prng_fill_u32, \
+from . import GEN_NAMES, LUXURY_P, PLANAR_P, prng_create, prng_destroy, prng_fill_f32, prng_fill_u32, \
     prng_get_tile, prng_set_tile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -71,7 +71,7 @@ def time_fill(gen: str, tile, n_streams: int, n_per: int, luxury: int = 0, dtype
     return ts[len(ts) // 2]
 
 
-def tune(gens=GEN_NAMES, luxuries=LUXURY_P, reps: int = 5, verbose: bool = True) -> dict:
+def tune(gens=GEN_NAMES, luxuries=LUXURY_P + PLANAR_P[1:], reps: int = 5, verbose: bool = True) -> dict:
     """Time every compiled tile and return {key: {"tile": [...], "ms": {...}}}."""
     result = {}
     jobs = []

@@ -11,6 +11,7 @@ import numpy as np
 SEED_BASE = 0x5EED            # stream i of a handle is seeded from splitmix64(0x5EED + i)
 GENS = ("ggl", "xor128", "ranecu", "ranmar", "ranlux", "mt19937")
 LUXURY_LEVELS = (24, 48, 97, 223, 389)
+PLANAR_LEVELS = (120, 240, 408)     # Section 3.6 planar scheme (its p = 48 is standard too)
 
 # Bulk fills (streams x draws per stream).
 SMALL = dict(n_streams=256, n_per=4096)                 # every element checked

@@ -27,6 +27,9 @@ int main(int argc, char** argv) {
   else if (!std::strcmp(name, "ranlux_p97")) dump(std::discard_block_engine<std::ranlux24_base, 97, 24>(seed), n);
   else if (!std::strcmp(name, "ranlux_p223")) dump(std::discard_block_engine<std::ranlux24_base, 223, 24>(seed), n);
   else if (!std::strcmp(name, "ranlux_p389")) dump(std::discard_block_engine<std::ranlux24_base, 389, 24>(seed), n);
+  else if (!std::strcmp(name, "ranlux_p120")) dump(std::discard_block_engine<std::ranlux24_base, 120, 24>(seed), n);
+  else if (!std::strcmp(name, "ranlux_p240")) dump(std::discard_block_engine<std::ranlux24_base, 240, 24>(seed), n);
+  else if (!std::strcmp(name, "ranlux_p408")) dump(std::discard_block_engine<std::ranlux24_base, 408, 24>(seed), n);
   else if (!std::strcmp(name, "lcg40014")) dump(lcg1(seed), n);
   else if (!std::strcmp(name, "lcg40692")) dump(lcg2(seed), n);
   else return 3;

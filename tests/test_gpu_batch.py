@@ -64,7 +64,7 @@ def test_batch_matches_oracle_mixed_requests():
             P.prng_destroy(h)
 
 
-@pytest.mark.parametrize("lux", [24, 97, 389])
+@pytest.mark.parametrize("lux", [24, 97, 389, 240])
 def test_batch_continues_handles_like_solo_fills(lux):
     # Two handles per generator: one filled through a batch launched three
     # times (re-seeded only by creation), its twin by plain fills.

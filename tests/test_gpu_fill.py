@@ -69,7 +69,7 @@ def test_small_config_every_element(gen):
     np.testing.assert_array_equal(got_f.view(np.uint32), ref_f.view(np.uint32))
 
 
-@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS)
+@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS + inputs.PLANAR_LEVELS)
 def test_ranlux_luxury_levels_small(p):
     ns, nper = 96, 1000
     ref = oracle.fill("ranlux", 99, ns, nper, luxury=p)
@@ -275,7 +275,7 @@ def test_roofline_config_mt_sampled(dtype):
     _sampled_rows_check("mt19937", 0, cfg["n_streams"], cfg["n_per"], 8, dtype)
 
 
-@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS)
+@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS + inputs.PLANAR_LEVELS)
 def test_luxury_sweep_config_sampled(p):
     cfg = inputs.LUX_SWEEP
     _sampled_rows_check("ranlux", p, cfg["n_streams"], cfg["n_per"], 8, "f32")

@@ -85,7 +85,7 @@ def test_swb_core_equals_ranlux24_base(stdlib_engines, seed):
     np.testing.assert_array_equal(got.astype(np.uint64), ref)
 
 
-@pytest.mark.parametrize("p", [48, 97, 223, 389])
+@pytest.mark.parametrize("p", [48, 97, 223, 389, 120, 240, 408])
 @pytest.mark.parametrize("seed", [19780503, 314159265])
 def test_ranlux_equals_discard_block(stdlib_engines, p, seed):
     ref = stdlib_engines(f"ranlux_p{p}", seed, 1500)
@@ -101,6 +101,14 @@ def test_luxury_levels(level, p):
     b = oracle.explicit_draws("ranlux", [77], 300, luxury=p)
     np.testing.assert_array_equal(a, b)
     assert oracle.luxury_p(5) == -1 and oracle.luxury_p(100) == -1
+
+
+@pytest.mark.parametrize("discard,p", [(24, 48), (96, 120), (216, 240), (384, 408)])
+def test_planar_luxury_p(discard, p):
+    # Section 3.6's planar scheme discards 24, 96, 216, 384 after each 24
+    # delivered numbers: p = 24 + discard, accepted as p itself.
+    assert p == 24 + discard
+    assert oracle.luxury_p(p) == p
 
 
 @pytest.mark.parametrize("s1,s2", [(1, 1), (12345, 67890), (M1 - 1, M2 - 1), (40014, 2)])
@@ -201,7 +209,7 @@ def test_xor128_gf2_linearity():
 
 # ---------------------------------------------------------------- RANLUX decimation
 
-@pytest.mark.parametrize("p", [48, 97, 223, 389])
+@pytest.mark.parametrize("p", [48, 97, 223, 389, 120, 240, 408])
 def test_ranlux_is_decimated_core(p):
     # Appendix A, "RANLUX": deliver 24 core values, discard p-24, repeat.
     blocks = 12

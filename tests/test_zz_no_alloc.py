@@ -20,7 +20,7 @@ import paper_1003_1898_gb300 as P  # noqa: E402
 
 SPECS = [("ggl", 0, 33, 130), ("xor128", 0, 129, 77), ("ranecu", 0, 7, 1000),
          ("ranmar", 0, 70, 150), ("ranlux", 223, 131, 61), ("ranlux", 24, 5, 100),
-         ("mt19937", 0, 9, 700)]
+         ("ranlux", 408, 3, 50), ("mt19937", 0, 9, 700)]
 
 
 @pytest.fixture(scope="module", autouse=True)
