@@ -72,6 +72,8 @@ def lib():
             L.orc_modpow.argtypes = [u64, u64, u64]
             L.orc_ggl_jump.restype = u32
             L.orc_ggl_jump.argtypes = [u32, u64]
+            L.orc_xor128_jump.restype = None
+            L.orc_xor128_jump.argtypes = [vp, u64]
             L.orc_serial_sample.restype = ctypes.c_int
             L.orc_serial_sample.argtypes = [i32, u64, vp, u64, vp]
             L.orc_serial_fill.restype = ctypes.c_int
@@ -163,6 +165,13 @@ def modpow(a: int, e: int, m: int) -> int:
 
 def ggl_jump(x: int, k: int) -> int:
     return int(lib().orc_ggl_jump(x, k))
+
+
+def xor128_jump(state, k: int):
+    """XOR128 state (x, y, z, w) after k steps, by the GF(2) matrix power."""
+    s = np.ascontiguousarray(np.asarray(state, dtype=np.uint32).copy())
+    lib().orc_xor128_jump(s.ctypes.data, k & (2**64 - 1))
+    return s
 
 
 def serial_sample(gen, x0: int, positions):

@@ -436,6 +436,59 @@ void orc_ranecu_jump(orc_ranecu *s, uint64_t k) {
   s->s2 = (int32_t)((a2 * (uint64_t)s->s2) % 2147483399ull);
 }
 
+/* XOR128 jump-ahead over GF(2) (Appendix A, "XORShift", matrix form): the
+ * state (x, y, z, w) is a 128-bit vector v (bit 32 i + b = bit b of word i,
+ * words in the order x, y, z, w) and one step is v <- T v for the 128 x 128
+ * block matrix T, so k steps are v <- T^k v.  T is taken column by column
+ * from the scalar step applied to the unit vectors (column j = T e_j), and
+ * T^k by square-and-multiply of 128 x 128 matrices over GF(2). */
+typedef struct { uint32_t col[128][4]; } orc_gf2_128;
+
+static void orc_gf2_apply(const orc_gf2_128 *A, const uint32_t v[4], uint32_t out[4]) {
+  uint32_t r[4] = {0, 0, 0, 0};
+  for (int j = 0; j < 128; j++)
+    if ((v[j / 32] >> (j % 32)) & 1u)
+      for (int i = 0; i < 4; i++) r[i] ^= A->col[j][i];
+  for (int i = 0; i < 4; i++) out[i] = r[i];
+}
+
+static void orc_gf2_mul(const orc_gf2_128 *A, const orc_gf2_128 *B, orc_gf2_128 *C) {
+  orc_gf2_128 t;
+  for (int j = 0; j < 128; j++) orc_gf2_apply(A, B->col[j], t.col[j]);
+  *C = t;
+}
+
+void orc_xor128_jump(orc_xor128 *s, uint64_t k) {
+  orc_gf2_128 T, R;
+  for (int j = 0; j < 128; j++) {
+    orc_xor128 e;
+    uint32_t unit[4] = {0, 0, 0, 0};
+    unit[j / 32] = 1u << (j % 32);
+    orc_xor128_init(&e, unit[0], unit[1], unit[2], unit[3]);
+    orc_xor128_next(&e);
+    T.col[j][0] = e.x; T.col[j][1] = e.y; T.col[j][2] = e.z; T.col[j][3] = e.w;
+    for (int i = 0; i < 4; i++) R.col[j][i] = (i == j / 32) ? (1u << (j % 32)) : 0u;
+  }
+  while (k > 0) {  /* R = T^k */
+    if (k & 1) orc_gf2_mul(&T, &R, &R);
+    orc_gf2_mul(&T, &T, &T);
+    k >>= 1;
+  }
+  uint32_t v[4] = {s->x, s->y, s->z, s->w}, o[4];
+  orc_gf2_apply(&R, v, o);
+  s->x = o[0]; s->y = o[1]; s->z = o[2]; s->w = o[3];
+}
+
+/* XOR128 state that the stream seeding map (reading R1) gives for the
+ * per-stream value s: (x, y) = (lo32 s, hi32 s), (z, w) = halves of
+ * splitmix64(s), w = 1 if all four are zero. */
+static void orc_xor128_from_s(orc_xor128 *x, uint64_t s) {
+  uint64_t t = orc_splitmix64(s);
+  uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32), z = (uint32_t)t, w = (uint32_t)(t >> 32);
+  if (lo == 0 && hi == 0 && z == 0 && w == 0) w = 1;
+  orc_xor128_init(x, lo, hi, z, w);
+}
+
 static int orc_serial_start(orc_stream *st, int32_t gen, uint64_t x0) {
   memset(st, 0, sizeof(*st));
   st->gen = gen;
@@ -448,6 +501,10 @@ static int orc_serial_start(orc_stream *st, int32_t gen, uint64_t x0) {
     uint64_t s1 = x0 & 0xFFFFFFFFull, s2 = x0 >> 32;
     if (s1 == 0 || s1 >= 2147483563ull || s2 == 0 || s2 >= 2147483399ull) return -1;
     orc_ranecu_init(&st->s.e, (int32_t)s1, (int32_t)s2);
+    return 0;
+  }
+  if (gen == ORC_XOR128) {
+    orc_xor128_from_s(&st->s.x, x0);
     return 0;
   }
   return -1;

@@ -108,9 +108,13 @@ uint64_t orc_modpow(uint64_t a, uint64_t e, uint64_t m);
  * component separately. */
 uint32_t orc_ggl_jump(uint32_t x, uint64_t k);
 void orc_ranecu_jump(orc_ranecu *s, uint64_t k);
+/* XOR128 jump-ahead: the state after k steps, T^k v over GF(2) with T the
+ * 128 x 128 matrix of one step (Appendix A, "XORShift", matrix form). */
+void orc_xor128_jump(orc_xor128 *s, uint64_t k);
 
 /* The single serial sequence started at x0 (GGL: x0 = seed value; RANECU:
- * x0 = s1 | s2 << 32): out[j] = draw j+1.  Returns the draws at sorted
+ * x0 = s1 | s2 << 32; XOR128: the state the stream seeding map gives for the
+ * per-stream value s = x0): out[j] = draw j+1.  Returns the draws at sorted
  * 0-based positions pos[0..n_pos) by stepping serially. */
 int orc_serial_sample(int32_t gen, uint64_t x0, const uint64_t *pos,
                       uint64_t n_pos, uint32_t *out_u32);

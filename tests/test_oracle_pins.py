@@ -172,19 +172,46 @@ def _word(b):
     return int(sum(int(v) << i for i, v in enumerate(b)))
 
 
-def test_xor128_matrix_form():
+def _xor128_paper_matrix():
     # Appendix A, "XORShift": the state row (X_{n-4}, ..., X_{n-1}) is mapped by
     # a 4x4 block matrix whose last column holds (I+L^11)(I+R^8) for X_{n-4}
     # and (I+R^19) for X_{n-1}; the other blocks shift the window.  Built here
-    # as a 128x128 GF(2) matrix and iterated independently of the scalar code.
+    # as a 128x128 GF(2) matrix (acting on column vectors, bit 32 i + b = bit b
+    # of word i, words x, y, z, w), independently of the scalar code.
     I = np.eye(32, dtype=np.uint8)
     A = ((I ^ _shift_mat(8, False)) @ (I ^ _shift_mat(11, True))) % 2
     B = (I ^ _shift_mat(19, False)) % 2
     Z = np.zeros((32, 32), dtype=np.uint8)
-    T = np.block([[Z, I, Z, Z],
-                  [Z, Z, I, Z],
-                  [Z, Z, Z, I],
-                  [A, Z, Z, B]]).astype(np.int64)
+    return np.block([[Z, I, Z, Z],
+                     [Z, Z, I, Z],
+                     [Z, Z, Z, I],
+                     [A, Z, Z, B]]).astype(np.int64)
+
+
+def _gf2_matmul(a, b):
+    return (a @ b) % 2
+
+
+def _gf2_pow(m, k):
+    r = np.eye(m.shape[0], dtype=np.int64)
+    while k:
+        if k & 1:
+            r = _gf2_matmul(m, r)
+        m = _gf2_matmul(m, m)
+        k >>= 1
+    return r
+
+
+def _vec(words):
+    return np.concatenate([_bits(int(w)) for w in words]).astype(np.int64)
+
+
+def _words(v):
+    return [_word(v[32 * i:32 * i + 32]) for i in range(4)]
+
+
+def test_xor128_matrix_form():
+    T = _xor128_paper_matrix()
     rng = random.Random(14)
     for _ in range(8):
         words = [rng.getrandbits(32) for _ in range(4)]
@@ -205,6 +232,54 @@ def test_xor128_gf2_linearity():
         sb = oracle.explicit_draws("xor128", b, 64)
         sab = oracle.explicit_draws("xor128", ab, 64)
         np.testing.assert_array_equal(sab, sa ^ sb)
+
+
+# ---------------------------------------------------------------- XOR128 jump-ahead
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 31, 100, 4096, 65537])
+def test_xor128_jump_equals_stepping(k):
+    # Brute force: the next draws from the jumped state are draws k+1, k+2, ...
+    rng = random.Random(k + 3)
+    for _ in range(3):
+        st = [rng.getrandbits(32) for _ in range(4)]
+        serial = oracle.explicit_draws("xor128", st, k + 8)
+        jumped = oracle.xor128_jump(st, k)
+        np.testing.assert_array_equal(oracle.explicit_draws("xor128", jumped, 8), serial[k:k + 8])
+
+
+def test_xor128_jump_matches_paper_matrix_power():
+    # T^k of the paper's block matrix by independent numpy square-and-multiply.
+    T = _xor128_paper_matrix()
+    rng = random.Random(16)
+    for _ in range(6):
+        k = rng.getrandbits(64)
+        st = [rng.getrandbits(32) for _ in range(4)]
+        want = _words((_gf2_pow(T, k) @ _vec(st)) % 2)
+        assert [int(x) for x in oracle.xor128_jump(st, k)] == want
+
+
+def test_xor128_jump_period():
+    # The period divides 2^128 - 1 (Appendix A, "XORShift"): T^(2^128) = T.
+    # N = T^(2^63) is read off the oracle's jump of the 128 unit vectors, then
+    # squared 65 times here; it must come back to T itself.
+    def unit(j):
+        w = [0, 0, 0, 0]
+        w[j // 32] = 1 << (j % 32)
+        return w
+    cols = [_vec(oracle.xor128_jump(unit(j), 2**63)) for j in range(128)]
+    n = np.stack(cols, axis=1).astype(np.int64)
+    for _ in range(65):
+        n = _gf2_matmul(n, n)
+    np.testing.assert_array_equal(n, _xor128_paper_matrix())
+
+
+def test_xor128_serial_start_is_the_seeding_map():
+    # Reading R1 for s = x0: (x, y) = halves of x0, (z, w) = halves of splitmix64(x0).
+    for x0 in (1, 12345, 2**63 + 11):
+        t = oracle.splitmix64(x0)
+        st = [x0 & 0xFFFFFFFF, x0 >> 32, t & 0xFFFFFFFF, t >> 32]
+        np.testing.assert_array_equal(oracle.serial_fill("xor128", x0, 50),
+                                      oracle.explicit_draws("xor128", st, 50))
 
 
 # ---------------------------------------------------------------- RANLUX decimation
