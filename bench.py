@@ -254,6 +254,36 @@ LUX_STREAMS, LUX_PER = 65536, 4096
 INT_LANES_PER_SM = 64      # 32-bit integer ALU lanes per SM per clock (half the FP32 rate)
 
 
+def _time_ms(torch, stream, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def measure_xor128_jump(P, torch, out_u, h_xor, stream):
+    """XOR128 jump-ahead over GF(2): the single-sequence fill of 2^30 draws
+    in 65,536 chunks (chunk starts by doubling passes of T^L, then the
+    ordinary fill), and prng_skip(2^40) of the 131,072-stream handle."""
+    sid = stream.cuda_stream
+    x0 = SEED
+    ms = _time_ms(torch, stream, lambda: P.prng_fill_jump_u32("xor128", x0, JUMP_N, JUMP_CHUNKS,
+                                                               out_u.data_ptr(), sid))
+    byt = 4 * JUMP_N
+    skip_ms = _time_ms(torch, stream, lambda: P.prng_skip(h_xor, 2**40, sid))
+    return {"fill": {"numbers": JUMP_N, "chunks": JUMP_CHUNKS, "ms": ms,
+                     "numbers_per_s": JUMP_N / (ms / 1e3), "gbs": byt / (ms / 1e3) / 1e9,
+                     "frac_hbm": byt / (ms / 1e3) / 1e9 / peaks()[0]},
+            "skip_2p40": {"streams": N_STREAMS, "ms": skip_ms}}
+
+
 def measure_luxury_sweep(P, torch, dev, stream, sm_mhz):
     """ns/number of RANLUX f32 fills (2^28 over 65,536 streams) for every
     standard p, and the fraction of the integer-pipe bound reached.  The
@@ -400,6 +430,7 @@ def run_ours(args, rank, world, local_rank):
     # RANLUX luxury sweep: 2^28 f32 per p over 65,536 streams, against the
     # integer-pipe bound of the subtract-with-borrow chains.
     lux_sweep = measure_luxury_sweep(P, torch, dev, stream, clk.summary().get("sm_mhz"))
+    xor128_jump = measure_xor128_jump(P, torch, out_u, handles["xor128"], stream)
 
     # Batched requests (20,000 mixed fills): one graph launch vs one plain
     # re-seed + fill per request.
@@ -455,6 +486,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline_all_cores": cpu_mt,
         "per_kernel": per,
         "luxury_sweep": lux_sweep,
+        "xor128_jump": xor128_jump,
         "tiles": {"tuned_cache": bool(tuned),
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }

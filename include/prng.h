@@ -92,7 +92,9 @@ int prng_fill_f32(prng_state *st, float *d_out, uint64_t n_per_stream, void *str
 
 /* Advance every stream by k draws without writing them (same result as a
  * fill of k whose output is thrown away).  GGL and RANECU jump in O(log k)
- * by a^k mod m (Appendix A, eq. MLCG); the others step. */
+ * by a^k mod m (Appendix A, eq. MLCG); XOR128 (k >= 256) by T^k, the k-th
+ * power of its 128 x 128 step matrix over GF(2) (Appendix A, "XORShift",
+ * matrix form), formed on the host in O(log k); the others step. */
 int prng_skip(prng_state *st, uint64_t k, void *stream);
 
 /* Checkpoint.  prng_get_state copies the handle's full state into h_buf
@@ -105,13 +107,20 @@ int prng_skip(prng_state *st, uint64_t k, void *stream);
 int prng_get_state(prng_state *st, void *h_buf, size_t *bytes);
 int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
 
-/* Single-sequence jump-ahead fill (GGL and RANECU only): write draws 1..n of
- * the one sequence started at x0 to d_out[0..n), computed as n_chunks
- * contiguous chunks in parallel, chunk c starting from a^(c*L) x0 mod m,
- * L = ceil(n / n_chunks), by square-and-multiply (Appendix A, eq. MLCG).
- * GGL: x0 in [1, 2^31-2].  RANECU: x0 = s1 | (s2 << 32) with s1 in
- * [1, m1-1], s2 in [1, m2-1], both components jumped separately.  Other
- * generators return PRNG_EUNSUPPORTED. */
+/* Single-sequence jump-ahead fill (GGL, RANECU and XOR128): write draws
+ * 1..n of the one sequence started at x0 to d_out[0..n), computed as
+ * n_chunks contiguous chunks in parallel, L = ceil(n / n_chunks) draws each.
+ * GGL: x0 in [1, 2^31-2], chunk c starts from a^(c*L) x0 mod m by
+ * square-and-multiply (Appendix A, eq. MLCG).  RANECU: x0 = s1 | (s2 << 32)
+ * with s1 in [1, m1-1], s2 in [1, m2-1], both components jumped separately.
+ * XOR128: any x0; the sequence starts from the state the stream seeding map
+ * gives for the per-stream value s = x0 ((x, y) = halves of x0, (z, w) =
+ * halves of splitmix64(x0)), and chunk c starts from T^(c*L) of it over
+ * GF(2) (Appendix A, "XORShift", matrix form).  The XOR128 form may cut the
+ * sequence into more, shorter chunks than asked (at least 131072 when n
+ * allows 64 draws each; the output is the same), and allocates a
+ * stream-ordered scratch array of 16 bytes per chunk (PRNG_EALLOC if that
+ * fails).  Other generators return PRNG_EUNSUPPORTED. */
 int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        uint32_t *d_out, void *stream);
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,

@@ -55,11 +55,19 @@ int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t
 int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
               cudaStream_t s) {
   if (gen < 0 || gen > 5) return PRNG_EGEN;
-  if (gen != GGL && gen != RANECU) return PRNG_EUNSUPPORTED;
+  if (gen != GGL && gen != RANECU && gen != XOR128) return PRNG_EUNSUPPORTED;
   if (n == 0) return PRNG_OK;
   if (d_out == nullptr) return PRNG_ENULL;
   if (n_chunks == 0) return PRNG_ESIZE;
   if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
+  if (gen == XOR128) {  // every 64-bit x0 is a valid seeding value
+    const cudaError_t e = launch_jump_xor128(x0, n, n_chunks, d_out, f32, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? PRNG_EALLOC : PRNG_ECUDA;
+    }
+    return PRNG_OK;
+  }
   if (gen == GGL) {
     if (x0 == 0 || x0 >= 2147483647ull) return PRNG_ESEED;
   } else {
@@ -189,6 +197,10 @@ int prng_fill_f32(prng_state* st, float* d_out, uint64_t n_per_stream, void* str
   return fill_impl(st, d_out, n_per_stream, 1, static_cast<cudaStream_t>(stream));
 }
 
+// XOR128 skips of at least this many steps use the GF(2) matrix power
+// (about 128 column XORs per stream) instead of stepping.
+constexpr uint64_t kXor128MatrixSkip = 256;
+
 int prng_skip(prng_state* st, uint64_t k, void* stream) {
   if (st == nullptr) return PRNG_ENULL;
   if (k == 0) return PRNG_OK;
@@ -196,6 +208,8 @@ int prng_skip(prng_state* st, uint64_t k, void* stream) {
   cudaError_t e;
   if (st->gen == GGL || st->gen == RANECU) {
     e = launch_skip_mlcg(st->gen, st->d_state, st->n_streams, k, s);
+  } else if (st->gen == XOR128 && k >= kXor128MatrixSkip) {
+    e = launch_skip_xor128(st->d_state, st->n_streams, k, s);
   } else {
     FillDesc d{};
     d.state = st->d_state;

@@ -63,6 +63,20 @@ cudaError_t launch_skip_mlcg(int gen, uint32_t* state, uint64_t n, uint64_t k,
 
 Tile default_tile(int gen, int p);
 
+// SplitMix64 (Steele, Lea, Flood 2014): gamma increment, then mix64.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// XOR128 jump-ahead over GF(2): prng_skip of k steps on a handle's state
+// (struct-of-arrays [4][n]), and the single-sequence chunked fill.
+cudaError_t launch_skip_xor128(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s);
+cudaError_t launch_jump_xor128(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
+                               cudaStream_t s);
+
 // ------------------------------------------------------------------ device
 
 __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }

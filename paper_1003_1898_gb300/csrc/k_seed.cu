@@ -14,14 +14,6 @@
 
 namespace prng {
 
-// SplitMix64 (Steele, Lea, Flood 2014): gamma increment, then mix64.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-  uint64_t z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // RMARIN (James 1988, cited by Section 3.5): 97 entries of 24 bits, most
 // significant bit first, from the lagged product generator mod 179 and the
 // LCG (53 l + 1) mod 169.  Written in canonical order V[k] = U[97 - k].

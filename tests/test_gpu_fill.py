@@ -141,6 +141,46 @@ def test_skip_equals_discarded_fill(gen):
         np.testing.assert_array_equal(got, ref, err_msg=f"skip {k}")
 
 
+def _xor128_seeded(seed, i):
+    # Reading R1 for XOR128: s = splitmix64(seed + i), (x, y) = halves of s,
+    # (z, w) = halves of splitmix64(s).
+    s = oracle.splitmix64(seed + i)
+    t = oracle.splitmix64(s)
+    return [s & 0xFFFFFFFF, s >> 32, t & 0xFFFFFFFF, t >> 32]
+
+
+@pytest.mark.parametrize("k", [256, 1000, 65537, 2**40 + 7, 2**64 - 1])
+def test_xor128_skip_by_matrix_power(k):
+    # Skips of 256 or more run as T^k over GF(2); checked against the
+    # oracle's own GF(2) jump of each stream's seeded state.
+    ns, nper = 300, 37
+    h = P.prng_create("xor128", 11, ns, 0)
+    try:
+        P.prng_skip(h, k)
+        got = u32(fill(h, ns, nper))
+    finally:
+        P.prng_destroy(h)
+    for i in range(ns):
+        st = oracle.xor128_jump(_xor128_seeded(11, i), k)
+        np.testing.assert_array_equal(got[i], oracle.explicit_draws("xor128", st, nper),
+                                      err_msg=f"stream {i}")
+
+
+def test_xor128_skip_matrix_equals_stepping():
+    # The same skip on the two sides of the switch: 300 = 255 + 45 steps.
+    ns, nper = 129, 20
+    a = P.prng_create("xor128", 3, ns, 0)
+    b = P.prng_create("xor128", 3, ns, 0)
+    try:
+        P.prng_skip(a, 300)
+        P.prng_skip(b, 255)
+        P.prng_skip(b, 45)
+        np.testing.assert_array_equal(u32(fill(a, ns, nper)), u32(fill(b, ns, nper)))
+    finally:
+        P.prng_destroy(a)
+        P.prng_destroy(b)
+
+
 @pytest.mark.parametrize("gen", inputs.GENS)
 def test_misaligned_output_scalar_path(gen):
     # Output starting 1 element past a 16-byte boundary forces the scalar
@@ -204,7 +244,7 @@ def test_zero_length_fill_is_noop():
 
 # ------------------------------------------------------------ jump-ahead
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
 @pytest.mark.parametrize("n,chunks", [(1, 1), (1000, 7), (100003, 37), (65536, 65536), (50000, 1)])
 def test_jump_fill_small_every_element(gen, n, chunks):
     x0 = inputs.JUMP_X0[gen]
@@ -221,9 +261,9 @@ def test_jump_fill_small_every_element(gen, n, chunks):
                                   oracle.to_f32(gen, ref).view(np.uint32))
 
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
 def test_jump_fill_other_start(gen):
-    x0 = 123456789 if gen == "ggl" else (987654 | (13579 << 32))
+    x0 = {"ggl": 123456789, "ranecu": 987654 | (13579 << 32), "xor128": 0}[gen]
     n = 77777
     out = torch.empty((n,), dtype=torch.int32, device="cuda")
     P.prng_fill_jump_u32(gen, x0, n, 100, out.data_ptr())
@@ -281,7 +321,7 @@ def test_luxury_sweep_config_sampled(p):
     _sampled_rows_check("ranlux", p, cfg["n_streams"], cfg["n_per"], 8, "f32")
 
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu"])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
 def test_jump_full_size_sampled(gen):
     n, chunks = inputs.JUMP["n"], inputs.JUMP["n_chunks"]
     x0 = inputs.JUMP_X0[gen]
