@@ -95,6 +95,10 @@ def lib():
             L.orc_luxury_p.argtypes = [i32]
             L.orc_to_f32.restype = ctypes.c_float
             L.orc_to_f32.argtypes = [i32, u32]
+            L.orc_to_f64.restype = ctypes.c_double
+            L.orc_to_f64.argtypes = [i32, u32, u32]
+            L.orc_fill_f64.restype = ctypes.c_int
+            L.orc_fill_f64.argtypes = [i32, i32, u64, u64, u32, u64, u64, vp]
             L.orc_ranecu_comp1.restype = u32
             L.orc_ranecu_comp1.argtypes = [ctypes.POINTER(i32)]
             L.orc_ranecu_comp2.restype = u32
@@ -128,6 +132,23 @@ def fill(gen, seed: int, n_streams: int, n_per: int, *, luxury: int = 0,
     if rc != 0:
         raise ValueError("oracle fill rejected its arguments")
     return (u, f) if want_f32 else u
+
+
+def fill_f64(gen, seed: int, n_streams: int, n_per: int, *, luxury: int = 0,
+             stream0: int = 0, skip: int = 0):
+    """Doubles (reading R11) of streams [stream0, stream0+n_streams), each
+    made of two consecutive draws; shape (n_streams, n_per)."""
+    out = np.zeros((n_streams, n_per), dtype=np.float64)
+    rc = lib().orc_fill_f64(gen_id(gen), luxury, seed & (2**64 - 1), stream0, n_streams, skip,
+                            n_per, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle fill_f64 rejected its arguments")
+    return out
+
+
+def to_f64(gen, a, b):
+    L, g = lib(), gen_id(gen)
+    return np.array([L.orc_to_f64(g, int(x), int(y)) for x, y in zip(a, b)], dtype=np.float64)
 
 
 def sample(gen, seed: int, stream: int, positions, *, luxury: int = 0):

@@ -286,6 +286,24 @@ float orc_to_f32(int32_t gen, uint32_t v) {
   return (float)d;
 }
 
+/* Reading R11: a double from two consecutive draws (Section 3.1 and
+ * Section 4 ask for doubles built from several draws rather than a widened
+ * single one, without a rule).  The high part comes from the first draw a,
+ * the low part from the second draw b, both taken from the top of the
+ * generator's word:
+ *   24-bit words (RANMAR, RANLUX): (a 2^24 + b) 2^-48;
+ *   31-bit words (GGL, RANECU):    ((a >> 4) 2^26 + (b >> 5)) 2^-53;
+ *   32-bit words (XOR128, MT19937): ((a >> 5) 2^26 + (b >> 6)) 2^-53.
+ * The integer has at most 53 bits and the scale is a power of two, so the
+ * value is exact and lies in [0, 1). */
+double orc_to_f64(int32_t gen, uint32_t a, uint32_t b) {
+  if (gen == ORC_RANMAR || gen == ORC_RANLUX)
+    return ((double)a * 16777216.0 + (double)b) / 281474976710656.0;
+  int sa = 5, sb = 6;
+  if (gen == ORC_GGL || gen == ORC_RANECU) { sa = 4; sb = 5; }
+  return ((double)(a >> sa) * 67108864.0 + (double)(b >> sb)) / 9007199254740992.0;
+}
+
 /* ---------------------------------------------------------------- streams */
 
 /* Reading R1: s = splitmix64(seed + i), then
@@ -358,6 +376,21 @@ int orc_fill(int32_t gen, int32_t luxury, uint64_t seed, uint64_t stream0,
       uint32_t v = orc_stream_next(&st);
       if (out_u32) out_u32[i * n_per + k] = v;
       if (out_f32) out_f32[i * n_per + k] = orc_to_f32(gen, v);
+    }
+  }
+  return 0;
+}
+
+int orc_fill_f64(int32_t gen, int32_t luxury, uint64_t seed, uint64_t stream0,
+                 uint32_t n_streams, uint64_t skip, uint64_t n_per, double *out) {
+  orc_stream st;
+  for (uint64_t i = 0; i < n_streams; i++) {
+    if (orc_stream_seed(&st, gen, luxury, seed, stream0 + i) != 0) return -1;
+    for (uint64_t k = 0; k < skip; k++) orc_stream_next(&st);
+    for (uint64_t k = 0; k < n_per; k++) {
+      uint32_t a = orc_stream_next(&st);
+      uint32_t b = orc_stream_next(&st);
+      out[i * n_per + k] = orc_to_f64(gen, a, b);
     }
   }
   return 0;

@@ -82,6 +82,15 @@ float orc_to_f32(int32_t gen, uint32_t v);
 int orc_stream_seed(orc_stream *st, int32_t gen, int32_t luxury, uint64_t seed, uint64_t i);
 uint32_t orc_stream_next(orc_stream *st);
 
+/* Reading R11: the double made of the consecutive draws a then b (24-bit
+ * words: (a 2^24 + b) 2^-48; 31-bit: ((a >> 4) 2^26 + (b >> 5)) 2^-53;
+ * 32-bit: ((a >> 5) 2^26 + (b >> 6)) 2^-53), exact, in [0, 1). */
+double orc_to_f64(int32_t gen, uint32_t a, uint32_t b);
+/* Doubles of streams [stream0, stream0+n_streams) after `skip` draws:
+ * out[i n_per + k] = orc_to_f64 of draws 2k+1 and 2k+2 after the skip. */
+int orc_fill_f64(int32_t gen, int32_t luxury, uint64_t seed, uint64_t stream0,
+                 uint32_t n_streams, uint64_t skip, uint64_t n_per, double *out);
+
 /* Streams [stream0, stream0+n_streams) of a handle (gen, luxury, seed): each
  * stream first discards `skip` draws, then writes n_per draws, stream-major.
  * Either output pointer may be NULL.  Returns 0 or -1. */

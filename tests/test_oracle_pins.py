@@ -234,6 +234,42 @@ def test_xor128_gf2_linearity():
         np.testing.assert_array_equal(sab, sa ^ sb)
 
 
+# ---------------------------------------------------------------- doubles from pairs
+
+F64_RULE = {"ranmar": (0, 0, 24, 48), "ranlux": (0, 0, 24, 48),
+            "ggl": (4, 5, 26, 53), "ranecu": (4, 5, 26, 53),
+            "xor128": (5, 6, 26, 53), "mt19937": (5, 6, 26, 53)}
+
+
+@pytest.mark.parametrize("gen", list(F64_RULE))
+@pytest.mark.parametrize("skip", [0, 1, 24])
+def test_f64_pairs_of_the_u32_stream(gen, skip):
+    # Reading R11: double k of a stream is made of draws 2k+1 (high part) and
+    # 2k+2 (low part) after the skip; checked against the pinned u32 stream
+    # with Python integers (order of the pair, shifts and pairing offset).
+    sa, sb, wb, total = F64_RULE[gen]
+    lux = 223 if gen == "ranlux" else 0
+    n = 150
+    u = oracle.fill(gen, 0x5EED, 3, 2 * n, luxury=lux, skip=skip)
+    d = oracle.fill_f64(gen, 0x5EED, 3, n, luxury=lux, skip=skip)
+    for i in range(3):
+        for k in range(n):
+            a, b = int(u[i, 2 * k]), int(u[i, 2 * k + 1])
+            want = ((a >> sa) << wb) | (b >> sb)
+            got = d[i, k] * 2.0**total
+            assert got == float(want) and want < 2**total, (gen, i, k)
+    assert np.all(d >= 0.0) and np.all(d < 1.0)
+
+
+def test_f64_extremes():
+    # All-ones words give the largest value below 1; zero words give 0.
+    top = {"ranmar": 2**24 - 1, "ranlux": 2**24 - 1, "ggl": 2**31 - 1, "ranecu": 2**31 - 1,
+           "xor128": 2**32 - 1, "mt19937": 2**32 - 1}
+    for gen, (_, _, _, total) in F64_RULE.items():
+        assert oracle.to_f64(gen, [top[gen]], [top[gen]])[0] == 1.0 - 2.0**-total
+        assert oracle.to_f64(gen, [0], [0])[0] == 0.0
+
+
 # ---------------------------------------------------------------- XOR128 jump-ahead
 
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 31, 100, 4096, 65537])
