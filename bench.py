@@ -284,6 +284,23 @@ def measure_xor128_jump(P, torch, out_u, h_xor, stream):
             "skip_2p40": {"streams": N_STREAMS, "ms": skip_ms}}
 
 
+def measure_f64(P, torch, out_u, handles, seed_r, stream):
+    """Doubles from pairs of draws: 2^29 doubles (4 GiB) per generator on
+    the roofline handles, each double made of two draws; bytes per launch
+    are the 8-byte outputs plus the state read and write."""
+    sid = stream.cuda_stream
+    res = {}
+    for g in GENS:
+        ns, nper = shape(g)
+        P.prng_reseed(handles[g], seed_r[g], sid)
+        ms = _time_ms(torch, stream, lambda: P.prng_fill_f64(handles[g], out_u.data_ptr(), nper // 2, sid))
+        n = ns * (nper // 2)
+        byt = 8 * n + 2 * 4 * STATE_WORDS[g] * ns
+        res[g] = {"doubles": n, "ms": ms, "doubles_per_s": n / (ms / 1e3),
+                  "gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / peaks()[0]}
+    return res
+
+
 def measure_luxury_sweep(P, torch, dev, stream, sm_mhz):
     """ns/number of RANLUX f32 fills (2^28 over 65,536 streams) for every
     standard p, and the fraction of the integer-pipe bound reached.  The
@@ -431,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
     # integer-pipe bound of the subtract-with-borrow chains.
     lux_sweep = measure_luxury_sweep(P, torch, dev, stream, clk.summary().get("sm_mhz"))
     xor128_jump = measure_xor128_jump(P, torch, out_u, handles["xor128"], stream)
+    f64 = measure_f64(P, torch, out_u, handles, seed_r, stream)
 
     # Batched requests (20,000 mixed fills): one graph launch vs one plain
     # re-seed + fill per request.
@@ -487,6 +505,7 @@ def run_ours(args, rank, world, local_rank):
         "per_kernel": per,
         "luxury_sweep": lux_sweep,
         "xor128_jump": xor128_jump,
+        "f64": f64,
         "tiles": {"tuned_cache": bool(tuned),
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }

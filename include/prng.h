@@ -53,7 +53,8 @@ enum {
   PRNG_EUNSUPPORTED = -7,/* operation not defined for this generator             */
   PRNG_EBLOB = -8,       /* malformed or mismatched state blob                   */
   PRNG_ESEED = -9,       /* jump start value outside the generator's range       */
-  PRNG_ESCRATCH = -10    /* batch larger than prng_batch_fill_noalloc's fixed scratch */
+  PRNG_ESCRATCH = -10,   /* batch larger than prng_batch_fill_noalloc's fixed scratch */
+  PRNG_EPARITY = -11     /* f64 fill of RANLUX/MT19937 at an odd block position */
 };
 
 /* Opaque handle: one generator type, n_streams independent streams, their
@@ -89,6 +90,20 @@ int prng_reseed(prng_state *st, uint64_t seed, void *stream);
  * 16-byte alignment with n_per_stream % 4 == 0 takes the vector-store path. */
 int prng_fill_u32(prng_state *st, uint32_t *d_out, uint64_t n_per_stream, void *stream);
 int prng_fill_f32(prng_state *st, float *d_out, uint64_t n_per_stream, void *stream);
+
+/* Doubles from pairs of draws (Sections 3.1 and 4 ask for doubles built
+ * from several draws rather than a widened single one): element (i, j) of
+ * d_out (stream-major, n_streams * n_per_stream doubles) is made of draws
+ * 2j+1 (high part) and 2j+2 (low part) of stream i counted from this call,
+ * and every stream advances by 2 n_per_stream draws.  24-bit generators
+ * (RANMAR, RANLUX) give (a 2^24 + b) 2^-48; the others give the top 27
+ * bits of a over the top 26 bits of b, 2^-53 (31-bit words: (a >> 4) 2^26 +
+ * (b >> 5); 32-bit words: (a >> 5) 2^26 + (b >> 6)).  Every value is exact
+ * and in [0, 1).  d_out needs 8-byte alignment.  RANLUX and MT19937 need an
+ * even number of draws taken since seeding (their position inside the
+ * 24-draw block or the 624-word table must be even): PRNG_EPARITY
+ * otherwise, with nothing written. */
+int prng_fill_f64(prng_state *st, double *d_out, uint64_t n_per_stream, void *stream);
 
 /* Advance every stream by k draws without writing them (same result as a
  * fill of k whose output is thrown away).  GGL and RANECU jump in O(log k)

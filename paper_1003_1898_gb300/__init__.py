@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         "prng_reseed": ([vp, u64, vp], ctypes.c_int),
         "prng_fill_u32": ([vp, vp, u64, vp], ctypes.c_int),
         "prng_fill_f32": ([vp, vp, u64, vp], ctypes.c_int),
+        "prng_fill_f64": ([vp, vp, u64, vp], ctypes.c_int),
         "prng_skip": ([vp, u64, vp], ctypes.c_int),
         "prng_get_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "prng_set_state": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -139,6 +140,11 @@ def prng_fill_u32(h, out, n_per_stream: int, stream=None):
 
 def prng_fill_f32(h, out, n_per_stream: int, stream=None):
     _check(lib().prng_fill_f32(h, _ptr(out), n_per_stream, _stream(stream)), "prng_fill_f32")
+
+
+def prng_fill_f64(h, out, n_per_stream: int, stream=None):
+    """Doubles from pairs of draws: each stream advances by 2 n_per_stream."""
+    _check(lib().prng_fill_f64(h, _ptr(out), n_per_stream, _stream(stream)), "prng_fill_f64")
 
 
 def prng_skip(h, k: int, stream=None):
@@ -293,14 +299,17 @@ class Generator:
         return self._h
 
     def fill(self, n_per_stream: int, dtype: str = "u32", out=None, stream=None):
-        """Next n_per_stream draws of every stream as a (n_streams, n_per_stream)
-        CUDA tensor (int32 holding the u32 bits, or float32)."""
+        """Next n_per_stream outputs of every stream as a (n_streams,
+        n_per_stream) CUDA tensor: int32 holding the u32 bits, float32, or
+        float64 (each double made of two draws)."""
         import torch
         if out is None:
-            tdt = torch.float32 if dtype == "f32" else torch.int32
+            tdt = {"f32": torch.float32, "f64": torch.float64}.get(dtype, torch.int32)
             out = torch.empty((self.n_streams, n_per_stream), dtype=tdt, device="cuda")
         if dtype == "f32":
             prng_fill_f32(self._h, out, n_per_stream, stream)
+        elif dtype == "f64":
+            prng_fill_f64(self._h, out, n_per_stream, stream)
         else:
             prng_fill_u32(self._h, out, n_per_stream, stream)
         return out

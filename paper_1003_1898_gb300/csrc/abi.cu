@@ -20,11 +20,20 @@ namespace {
 constexpr uint32_t kBlobMagic = 0x50524E47u;  // "PRNG"
 constexpr uint32_t kBlobVersion = 1u;
 
-int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t s) {
+// n_per outputs per stream in output mode `mode`; doubles take two draws
+// each, so their fill runs the draw pipeline over 2 n_per draws.
+int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int mode, cudaStream_t s) {
   if (st == nullptr) return PRNG_ENULL;
   if (n_per == 0) return PRNG_OK;
   if (d_out == nullptr) return PRNG_ENULL;
-  if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
+  if ((reinterpret_cast<uintptr_t>(d_out) & (mode == OUT_F64 ? 7 : 3)) != 0) return PRNG_ESIZE;
+  if (mode == OUT_F64) {
+    if (n_per > UINT64_MAX / 2) return PRNG_ESIZE;
+    // RANLUX's block position and MT19937's table index must be even so
+    // that every pair sits inside the kernels' aligned units.
+    if ((st->gen == RANLUX || st->gen == MT19937) && (st->pos & 1)) return PRNG_EPARITY;
+    n_per *= 2;
+  }
   if (st->n_streams > UINT64_MAX / n_per) return PRNG_ESIZE;
   FillDesc d{};
   d.state = st->d_state;
@@ -35,7 +44,7 @@ int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int f32, cudaStream_t
   d.limit = UINT64_MAX;
   d.pos = st->pos;
   d.p = st->p;
-  d.f32 = f32;
+  d.mode = mode;
   d.jump = 0;
   const Tile t = default_tile(st->gen, st->p);
   cudaError_t e;
@@ -83,7 +92,7 @@ int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, 
   d.pitch = L;
   d.limit = n;
   d.x0 = x0;
-  d.f32 = f32;
+  d.mode = f32 ? OUT_F32 : OUT_U32;
   d.jump = 1;
   Tile t = default_tile(gen, 0);
   if (t.cols != 128) t = Tile{256, 128, 1};  // jump chunks always run lane-parallel
@@ -190,11 +199,15 @@ int prng_reseed(prng_state* st, uint64_t seed, void* stream) {
 }
 
 int prng_fill_u32(prng_state* st, uint32_t* d_out, uint64_t n_per_stream, void* stream) {
-  return fill_impl(st, d_out, n_per_stream, 0, static_cast<cudaStream_t>(stream));
+  return fill_impl(st, d_out, n_per_stream, OUT_U32, static_cast<cudaStream_t>(stream));
 }
 
 int prng_fill_f32(prng_state* st, float* d_out, uint64_t n_per_stream, void* stream) {
-  return fill_impl(st, d_out, n_per_stream, 1, static_cast<cudaStream_t>(stream));
+  return fill_impl(st, d_out, n_per_stream, OUT_F32, static_cast<cudaStream_t>(stream));
+}
+
+int prng_fill_f64(prng_state* st, double* d_out, uint64_t n_per_stream, void* stream) {
+  return fill_impl(st, d_out, n_per_stream, OUT_F64, static_cast<cudaStream_t>(stream));
 }
 
 // XOR128 skips of at least this many steps use the GF(2) matrix power
@@ -360,6 +373,7 @@ const char* prng_strerror(int code) {
     case PRNG_EBLOB: return "state blob does not match this handle";
     case PRNG_ESEED: return "start value outside the generator's range";
     case PRNG_ESCRATCH: return "batch exceeds the fixed scratch of prng_batch_fill_noalloc";
+    case PRNG_EPARITY: return "f64 fill of RANLUX or MT19937 at an odd draw position";
     default: return "unknown error code";
   }
 }

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace prng {
@@ -28,6 +29,22 @@ namespace prng {
 enum Gen : int { GGL = 0, XOR128 = 1, RANECU = 2, RANMAR = 3, RANLUX = 4, MT19937 = 5 };
 
 constexpr int kWords[6] = {1, 4, 2, 98, 25, 624};
+
+// Output of a fill.  OUT_F64 turns each pair of consecutive draws into one
+// double (reading R11): the kernels run the u32 pipeline over 2 n draws
+// per stream and convert each aligned pair (u32 slots 2k, 2k+1) into the
+// double that occupies the same 8 bytes.
+enum OutMode : int { OUT_U32 = 0, OUT_F32 = 1, OUT_F64 = 2 };
+
+// Calls fn(std::integral_constant<int, mode>) for a run-time mode.
+template <class Fn>
+inline auto with_mode(int mode, Fn&& fn) {
+  switch (mode) {
+    case OUT_F64: return fn(std::integral_constant<int, OUT_F64>{});
+    case OUT_F32: return fn(std::integral_constant<int, OUT_F32>{});
+    default: return fn(std::integral_constant<int, OUT_U32>{});
+  }
+}
 
 // One fill (or skip, or jump fill) as the kernels see it.
 struct FillDesc {
@@ -40,7 +57,7 @@ struct FillDesc {
   uint64_t x0;         // jump fills: start value (RANECU: s1 | s2 << 32)
   uint32_t pos;        // RANLUX: draws delivered from the current block; MT: mti
   int32_t p;           // RANLUX luxury p
-  int32_t f32;         // 1: write floats
+  int32_t mode;        // OutMode: u32 words, floats, or doubles from pairs
   int32_t jump;        // 1: rows are chunks of one jump-ahead sequence
 };
 
@@ -132,122 +149,54 @@ __device__ __forceinline__ void st_out4(uint32_t* p, uint4 v) {
   __stcs(reinterpret_cast<uint4*>(p), v);
 }
 
-// Copy a staged tile (rows [0, T) of `tile`, row pitch SP words, columns
-// [0, w)) to out rows row0.. at columns g0..: warp wi takes rows wi, wi+NW,
-// ...; its lanes take consecutive columns, so each warp store is one
-// contiguous run of the row.
-template <int T>
-__device__ __forceinline__ void copy_rows_scalar(const uint32_t* tile, int sp, uint32_t* out,
-                                                 uint64_t gpitch, uint64_t row0, uint64_t n_rows,
-                                                 uint64_t g0, int w, uint64_t limit) {
-  constexpr int NW = T / 32;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  for (int r = wi; r < T; r += NW) {
-    const uint64_t row = row0 + r;
-    if (row >= n_rows) break;
-    const uint64_t base = row * gpitch + g0;
-    for (int c = lane; c < w; c += 32)
-      if (base + c < limit) st_out(out + base + c, tile[r * sp + c]);
-  }
+// Double of the consecutive draws a (high part) then b (reading R11), for
+// generators whose words have WB significant bits: 24-bit words give
+// m 2^-48 with m = a 2^24 + b; 31- and 32-bit words give m 2^-53 with m =
+// (top 27 bits of a) 2^26 + (top 26 bits of b).  m has at most 53 bits, so
+// the value is exact.  The bits are assembled with 32-bit integer
+// instructions (the FP64 units of this GPU are slow): with the top bit of m
+// at q, the fraction is m shifted left to put that bit at 52 (a funnel shift
+// of its two words), and the exponent field 1022 + q - TOT is added to the
+// high word, the fraction's own bit 52 completing it to 1023 + q - TOT.
+// When the high part is zero (once in 2^24 or 2^27 pairs) a separate,
+// never-inlined FP64 conversion takes over, so the common path stays free
+// of FP64 instructions.
+static __device__ __noinline__ double pair_f64_low_only(uint32_t lo, double scale) {
+  return (double)lo * scale;
 }
 
-// Column-major staging tile of a thread-per-stream kernel: column c (the
-// c-th staged draw) of the CTA's row t sits at s[c * (T + 1) + t], so a
-// warp's 32 rows writing the same column hit 32 consecutive words (any
-// column, even one known only at run time), and the +1 skew keeps the
-// transposed reads below conflict-free.
-//
-// ColFlusher writes staged columns [0, w) to out at columns g0 .. g0 + w - 1
-// of rows row0 + t.  Lane (ro = lane & 3, qq = lane >> 2) handles row ro of
-// a 4-row group and 16-byte chunk qq of an 8-chunk group: four scalar
-// shared loads (banks 4 qq + ro + i, all distinct) and one 16-byte store,
-// so each warp store covers 4 rows x 128 contiguous bytes.  Chunks are
-// aligned to global multiples of 4 columns; a chunk cut by the edge of the
-// staged range, or a row base without 16-byte alignment, falls back to
-// scalar stores.  Row pointers and the per-lane row count are computed once
-// per kernel, so a flush is a short loop of loads and stores.
-// LIMITED: honour FillDesc::limit (batched requests whose last stream is
-// only partly wanted); single fills use the cheaper unlimited form.
-template <int T, bool LIMITED = false>
-struct ColFlusher {
-  static constexpr int SP = T + 1, NW = T / 32, RIT = T / (4 * NW);  // row groups per warp
-  uint32_t* gp;       // this lane's first row, column 0
-  uint64_t rowstep;   // elements between this lane's consecutive rows
-  const uint32_t* sp; // shared tile at this lane's first row
-  int nrow;           // rows of this lane with at least one element to write (<= RIT)
-  int kcut;           // index (< nrow) of the row cut by the element limit, or RIT
-  uint64_t ccut;      // columns of that row still below the limit
-  int qq;
-  bool vec_ok;
+template <int WB>
+__device__ __forceinline__ double pair_f64(uint32_t a, uint32_t b) {
+  constexpr int LB = WB == 24 ? 24 : 26, TOT = WB == 24 ? 48 : 53;
+  const uint32_t hi = WB == 24 ? a : a >> (WB - 27);
+  const uint32_t lo = WB == 24 ? b : b >> (WB - 26);
+  if (hi == 0) return pair_f64_low_only(lo, WB == 24 ? 0x1p-48 : 0x1p-53);
+  const int z = __clz(hi);                          // q = 31 - z + LB
+  const int s = 52 - (31 - z + LB);                 // 0 .. 28
+  const uint32_t mh = hi >> (32 - LB), ml = (hi << LB) | lo;
+  const uint32_t H = __funnelshift_l(ml, mh, s);    // high word of m << s
+  const uint32_t L = ml << s;
+  const uint32_t Hx = H + ((uint32_t)(1022 + 31 + LB - TOT - z) << 20);
+  return __hiloint2double((int)Hx, (int)L);
+}
 
-  // Rows row0 + r of `out` (pitch elements apart), writing only elements
-  // whose linear index is below `limit`.
-  __device__ __forceinline__ void init(const uint32_t* s, uint32_t* out, uint64_t pitch,
-                                       uint64_t row0, uint64_t n_rows, uint64_t limit) {
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int r = wi * 4 + (lane & 3);
-    qq = lane >> 2;
-    rowstep = (uint64_t)NW * 4 * pitch;
-    gp = out + (row0 + r) * pitch;
-    sp = s + r;
-    uint64_t rows = n_rows;                       // rows holding an element below the limit
-    if (LIMITED && pitch > 0 && (limit + pitch - 1) / pitch < rows) rows = (limit + pitch - 1) / pitch;
-    const uint64_t left = rows > row0 + r ? rows - (row0 + r) : 0;
-    const uint64_t nr = (left + (NW * 4 - 1)) / (NW * 4);
-    nrow = nr < (uint64_t)RIT ? (int)nr : RIT;
-    kcut = RIT;
-    ccut = 0;
-    if (LIMITED && pitch > 0 && limit < rows * pitch) {  // the last of those rows is partial
-      const uint64_t last = rows - 1;
-      if (last >= row0 + r && (last - (row0 + r)) % (NW * 4) == 0) {
-        kcut = (int)((last - (row0 + r)) / (NW * 4));
-        ccut = limit - last * pitch;
-      }
-    }
-    vec_ok = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  }
+// Stores of converted pairs at the u32 slot p of the pair's first draw
+// (8-byte aligned: pairs start at even slots of 8-byte-aligned rows).
+template <int WB>
+__device__ __forceinline__ void st_pair(uint32_t* p, uint32_t a, uint32_t b) {
+  __stcs(reinterpret_cast<double*>(p), pair_f64<WB>(a, b));
+}
+template <int WB>
+__device__ __forceinline__ void st_pair4(uint32_t* p, uint4 v) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(pair_f64<WB>(v.x, v.y), pair_f64<WB>(v.z, v.w)));
+}
 
-  __device__ __forceinline__ void flush(uint64_t g0, int w) const {
-    const uint64_t q0 = g0 >> 2;
-    const int nq = (int)(((g0 + (uint64_t)w + 3) >> 2) - q0);
-    for (int qb = 0; qb < nq; qb += 8) {
-      const int qi = qb + qq;
-      if (qi >= nq) continue;
-      const uint64_t gc = (q0 + qi) * 4;
-      const int c = (int)(gc - g0);
-      uint32_t* g = gp + gc;
-      if (vec_ok && c >= 0 && c + 4 <= w) {
-        const uint32_t* t = sp + c * SP;
-#pragma unroll
-        for (int k = 0; k < RIT; k++) {
-          if (k < nrow) {
-            uint4 v;
-            v.x = t[k * NW * 4];
-            v.y = t[k * NW * 4 + SP];
-            v.z = t[k * NW * 4 + 2 * SP];
-            v.w = t[k * NW * 4 + 3 * SP];
-            if (!LIMITED || k != kcut || gc + 4 <= ccut) {
-              st_out4(g + k * rowstep, v);
-            } else {
-              if (gc < ccut) st_out(g + k * rowstep, v.x);
-              if (gc + 1 < ccut) st_out(g + k * rowstep + 1, v.y);
-              if (gc + 2 < ccut) st_out(g + k * rowstep + 2, v.z);
-            }
-          }
-        }
-      } else {
-        for (int k = 0; k < nrow; k++) {
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            const int ci = c + i;
-            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
-              st_out(g + k * rowstep + i, sp[ci * SP + k * NW * 4]);
-          }
-        }
-      }
-    }
-  }
-};
+// A 16-byte chunk of four draws in output mode OM (pairs for OUT_F64).
+template <int OM, int WB>
+__device__ __forceinline__ void st_chunk(uint32_t* p, uint4 v) {
+  if constexpr (OM == OUT_F64) st_pair4<WB>(p, v);
+  else st_out4(p, v);
+}
 
 // Row-major staging tile: thread t's staged draws in row t (SPW words per
 // row, SPW = 4 mod 8 so that eight threads storing the same 16-byte chunk
@@ -258,8 +207,11 @@ struct ColFlusher {
 // multiple of 4 a chunk straddles two tile chunks and is assembled from two
 // 16-byte shared loads.  Eight lanes of a row read 128 contiguous bytes of
 // shared memory, and a warp store covers 4 rows x 128 bytes of the output.
-// LIMITED: honour FillDesc::limit (batched requests).
-template <int T, int SPW, bool LIMITED = false>
+// LIMITED: honour FillDesc::limit (batched requests).  OM == OUT_F64: the
+// staged words are raw draws of WB bits and each aligned pair (even global
+// column, the next one) leaves as one double; g0, w and the limit are then
+// even, so a pair is never split by a flush or a cut.
+template <int T, int SPW, bool LIMITED = false, int OM = OUT_U32, int WB = 32>
 struct RowFlusher {
   static_assert(SPW % 8 == 4, "row pitch must be 4 mod 8 words");
   static constexpr int NW = T / 32, RIT = T / (4 * NW);
@@ -325,15 +277,24 @@ struct RowFlusher {
             for (int i = 0; i < 4; i++) v[i] = u[A + i];
           }
           if (!LIMITED || k != kcut || gc + 4 <= ccut) {
-            st_out4(g + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
+            st_chunk<OM, WB>(g + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
             continue;
           }
         }
+        if constexpr (OM == OUT_F64) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int ci = c + i;
-          if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
-            st_out(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci]);
+          for (int i = 0; i < 4; i += 2) {
+            const int ci = c + i;
+            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
+              st_pair<WB>(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci], sp[k * NW * 4 * SPW + ci + 1]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            const int ci = c + i;
+            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
+              st_out(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci]);
+          }
         }
       }
     }
@@ -342,9 +303,9 @@ struct RowFlusher {
   __device__ __forceinline__ void flush(uint64_t g0, int w) const {
     switch ((uint32_t)(0u - (uint32_t)g0) & 3u) {
       case 0: flush_a<0>(g0, w); break;
-      case 1: flush_a<1>(g0, w); break;
       case 2: flush_a<2>(g0, w); break;
-      default: flush_a<3>(g0, w); break;
+      case 1: if constexpr (OM != OUT_F64) flush_a<1>(g0, w); break;
+      default: if constexpr (OM != OUT_F64) flush_a<3>(g0, w); break;
     }
   }
 };

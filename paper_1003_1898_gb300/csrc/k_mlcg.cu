@@ -49,10 +49,10 @@ struct RanecuLJ {
   }
 };
 
-template <class G, bool F32>
+template <class G, int OM>
 __device__ __forceinline__ uint32_t lj_conv(uint32_t v) {
-  if constexpr (F32) return as_f32_bits<G::SH>(v);
-  else return v;
+  if constexpr (OM == OUT_F32) return as_f32_bits<G::SH>(v);
+  else return v;   // u32, or a raw draw paired at the store
 }
 
 // Per-warp constants of one call: multipliers to a lane's first draw, to
@@ -72,7 +72,7 @@ struct LjConst {
 
 // One row (stream, or jump chunk whose start components are `base`) by one
 // warp: draws 0 .. nv-1 written to orow (row start), 16-byte stores when vec.
-template <class G, bool F32>
+template <class G, int OM>
 __device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&base)[G::NC], int lane,
                                        uint32_t* orow, uint64_t nv, bool vec) {
   constexpr int NC = G::NC;
@@ -84,15 +84,19 @@ __device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&bas
     uint32_t t[NC], o[4];
 #pragma unroll
     for (int c = 0; c < NC; c++) t[c] = s[c];
-    o[0] = lj_conv<G, F32>(G::out(t));
+    o[0] = lj_conv<G, OM>(G::out(t));
 #pragma unroll
     for (int i = 1; i < 4; i++) {
 #pragma unroll
       for (int c = 0; c < NC; c++) t[c] = G::step(c, t[c]);
-      o[i] = lj_conv<G, F32>(G::out(t));
+      o[i] = lj_conv<G, OM>(G::out(t));
     }
     if (vec && c0 + 128 <= nv) {
-      st_out4(orow + c0, make_uint4(o[0], o[1], o[2], o[3]));
+      st_chunk<OM, 31>(orow + c0, make_uint4(o[0], o[1], o[2], o[3]));
+    } else if constexpr (OM == OUT_F64) {   // nv is even: pairs are whole
+#pragma unroll
+      for (int i = 0; i < 4; i += 2)
+        if (c0 + 4 * lane + i < nv) st_pair<31>(orow + c0 + i, o[i], o[i + 1]);
     } else {
 #pragma unroll
       for (int i = 0; i < 4; i++)
@@ -105,7 +109,7 @@ __device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&bas
 
 // Stream `row` of a handle fill: load its state, write its row, store the
 // state advanced by n draws (lane 0).
-template <class G, bool F32>
+template <class G, int OM>
 __device__ __forceinline__ void lj_stream(const LjConst<G>& K, const FillDesc& d, uint64_t row, int lane) {
   constexpr int NC = G::NC;
   uint32_t base[NC];
@@ -115,14 +119,14 @@ __device__ __forceinline__ void lj_stream(const LjConst<G>& K, const FillDesc& d
   if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool vec = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  lj_row<G, F32>(K, base, lane, out + row * d.pitch, nv, vec);
+  lj_row<G, OM>(K, base, lane, out + row * d.pitch, nv, vec);
   if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < NC; c++) d.state[c * d.n_rows + row] = G::mul(c, base[c], K.fin_mul[c]);
   }
 }
 
-template <class G, int WPB, bool F32>
+template <class G, int WPB, int OM>
 __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
   constexpr int NC = G::NC;
   const int lane = threadIdx.x & 31;
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
   LjConst<G> K;
   K.init(lane, d.n_per);
   if (!d.jump) {
-    for (uint64_t row = wrow; row < d.n_rows; row += nwarps) lj_stream<G, F32>(K, d, row, lane);
+    for (uint64_t row = wrow; row < d.n_rows; row += nwarps) lj_stream<G, OM>(K, d, row, lane);
     return;
   }
   // Jump fill: chunk r starts at a^(r L) x0; this warp's chunks are nwarps apart.
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
   for (uint64_t row = wrow; row < d.n_rows; row += nwarps) {
     uint64_t nv = d.n_per;
     if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
-    lj_row<G, F32>(K, jrow, lane, out + row * d.pitch, nv, vec_ok && ((row * d.pitch) & 3) == 0);
+    lj_row<G, OM>(K, jrow, lane, out + row * d.pitch, nv, vec_ok && ((row * d.pitch) & 3) == 0);
 #pragma unroll
     for (int c = 0; c < NC; c++) jrow[c] = G::mul(c, jrow[c], jstep[c]);
   }
@@ -167,15 +171,15 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_mlcg(const BatchQueue q) {
       LjConst<GglLJ> K;
       K.init(lane, d.n_per);
       for (uint32_t k = 0; k < I.rows; k++) {
-        if (d.f32) lj_stream<GglLJ, true>(K, d, I.row0 + k, lane);
-        else lj_stream<GglLJ, false>(K, d, I.row0 + k, lane);
+        if (d.mode == OUT_F32) lj_stream<GglLJ, OUT_F32>(K, d, I.row0 + k, lane);
+        else lj_stream<GglLJ, OUT_U32>(K, d, I.row0 + k, lane);
       }
     } else {
       LjConst<RanecuLJ> K;
       K.init(lane, d.n_per);
       for (uint32_t k = 0; k < I.rows; k++) {
-        if (d.f32) lj_stream<RanecuLJ, true>(K, d, I.row0 + k, lane);
-        else lj_stream<RanecuLJ, false>(K, d, I.row0 + k, lane);
+        if (d.mode == OUT_F32) lj_stream<RanecuLJ, OUT_F32>(K, d, I.row0 + k, lane);
+        else lj_stream<RanecuLJ, OUT_U32>(K, d, I.row0 + k, lane);
       }
     }
   }
@@ -190,19 +194,21 @@ cudaError_t launch_batch_mlcg(const BatchQueue& q, Tile t, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class G, int WPB, bool F32>
+template <class G, int WPB, int OM>
 static cudaError_t launch_lj(const FillDesc& d, cudaStream_t s) {
   const uint64_t need = (d.n_rows + WPB - 1) / WPB;
   const uint64_t resident = (uint64_t)sm_count() * (2048 / (WPB * 32));
   const unsigned grid = (unsigned)(need < resident ? need : resident);
-  k_fill_lj<G, WPB, F32><<<grid, WPB * 32, 0, s>>>(d);
+  k_fill_lj<G, WPB, OM><<<grid, WPB * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 template <class G>
 static cudaError_t launch_lj_g(const FillDesc& d, Tile t, cudaStream_t s) {
-  if (t.threads == 256) return d.f32 ? launch_lj<G, 8, true>(d, s) : launch_lj<G, 8, false>(d, s);
-  return d.f32 ? launch_lj<G, 4, true>(d, s) : launch_lj<G, 4, false>(d, s);
+  return with_mode(d.mode, [&](auto m) {
+    return t.threads == 256 ? launch_lj<G, 8, decltype(m)::value>(d, s)
+                            : launch_lj<G, 4, decltype(m)::value>(d, s);
+  });
 }
 
 cudaError_t launch_fill_mlcg(int gen, const FillDesc& d, Tile t, cudaStream_t s) {

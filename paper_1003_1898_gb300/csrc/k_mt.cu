@@ -25,9 +25,9 @@ __device__ __forceinline__ uint32_t mt_temper(uint32_t t) {
 // its low byte cleared (at most 24 significant bits, so the conversion is
 // exact) times 2^-32.  The mask fuses with the last tempering XOR into one
 // three-input logic instruction, which the shift would not.
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ uint32_t mt_conv(uint32_t t) {
-  if constexpr (F32) return __float_as_uint(__uint2float_rn(t & 0xFFFFFF00u) * 0x1p-32f);
+  if constexpr (OM == OUT_F32) return __float_as_uint(__uint2float_rn(t & 0xFFFFFF00u) * 0x1p-32f);
   else return t;
 }
 
@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
 // Only the lane holding k = 224..227 straddles the switch.  Each new word is
 // tempered and, if o != null, written to o[k] (16-byte stores when VEC);
 // PARTIAL: only entries k < take are written.
-template <bool F32, bool PARTIAL>
+template <int OM, bool PARTIAL>
 __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec) {
 #pragma unroll
   for (int k0 = 0; k0 < 640; k0 += 128) {
@@ -76,17 +76,22 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
       *reinterpret_cast<uint4*>(s + k) = v;
       if (o != nullptr) {
         uint4 t;
-        t.x = mt_conv<F32>(mt_temper(v.x));
-        t.y = mt_conv<F32>(mt_temper(v.y));
-        t.z = mt_conv<F32>(mt_temper(v.z));
-        t.w = mt_conv<F32>(mt_temper(v.w));
+        t.x = mt_conv<OM>(mt_temper(v.x));
+        t.y = mt_conv<OM>(mt_temper(v.y));
+        t.z = mt_conv<OM>(mt_temper(v.z));
+        t.w = mt_conv<OM>(mt_temper(v.w));
         if (!PARTIAL && vec) {
-          st_out4(o + k, t);
+          st_chunk<OM, 32>(o + k, t);
         } else {
-          if (!PARTIAL || k < take) st_out(o + k, t.x);
-          if (!PARTIAL || k + 1 < take) st_out(o + k + 1, t.y);
-          if (!PARTIAL || k + 2 < take) st_out(o + k + 2, t.z);
-          if (!PARTIAL || k + 3 < take) st_out(o + k + 3, t.w);
+          if constexpr (OM == OUT_F64) {   // take and the table offset are even
+            if (!PARTIAL || k < take) st_pair<32>(o + k, t.x, t.y);
+            if (!PARTIAL || k + 2 < take) st_pair<32>(o + k + 2, t.z, t.w);
+          } else {
+            if (!PARTIAL || k < take) st_out(o + k, t.x);
+            if (!PARTIAL || k + 1 < take) st_out(o + k + 1, t.y);
+            if (!PARTIAL || k + 2 < take) st_out(o + k + 2, t.z);
+            if (!PARTIAL || k + 3 < take) st_out(o + k + 3, t.w);
+          }
         }
       }
     }
@@ -95,7 +100,7 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
 }
 
 // Stream `row` of a fill by one warp; s is the warp's 624-word table.
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane) {
   uint32_t* gs = d.state + row * 624;
   for (int k = lane; k < 624; k += 32) s[k] = gs[k];
@@ -115,31 +120,35 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
     const uint64_t h = (624 - mti) < n ? (624 - mti) : n;
     if (store)
       for (uint64_t k = lane; k < h && k < nv; k += 32)
-        st_out(orow + k, mt_conv<F32>(mt_temper(s[mti + k])));
+        if constexpr (OM == OUT_F64) {
+          if ((k & 1) == 0) st_pair<32>(orow + k, mt_temper(s[mti + k]), mt_temper(s[mti + k + 1]));
+        } else {
+          st_out(orow + k, mt_conv<OM>(mt_temper(s[mti + k])));
+        }
     j = h;
   }
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   const bool vec = store && ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   while (n - j >= 624) {
-    if (j + 624 <= nv) mt_twist<F32, false>(s, lane, store ? orow + j : nullptr, 624, vec);
-    else mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false);
+    if (j + 624 <= nv) mt_twist<OM, false>(s, lane, store ? orow + j : nullptr, 624, vec);
+    else mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false);
     j += 624;
   }
   if (j < n) {
     const uint64_t take = nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
-    mt_twist<F32, true>(s, lane, store ? orow + j : nullptr, (int)take, false);
+    mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)take, false);
   }
   for (int k = lane; k < 624; k += 32) gs[k] = s[k];
   __syncwarp();
 }
 
-template <int WPB, bool F32>
+template <int WPB, int OM>
 __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
   __shared__ __align__(16) uint32_t table[WPB][624];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const uint64_t row = (uint64_t)blockIdx.x * WPB + wi;
   if (row >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
-  mt_stream<F32>(d, row, table[wi], lane);
+  mt_stream<OM>(d, row, table[wi], lane);
 }
 
 // Batched MT19937 fills: each warp pops an item (up to 2 streams of one
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_mt(const BatchQueue q) {
     if (it >= q.n_items) break;
     const BatchItem I = q.items[it];
     const FillDesc& d = q.reqs[I.req].d;
-    for (uint32_t k = 0; k < I.rows; k++) mt_stream<F32>(d, I.row0 + k, table[wi], lane);
+    for (uint32_t k = 0; k < I.rows; k++) mt_stream<F32 ? OUT_F32 : OUT_U32>(d, I.row0 + k, table[wi], lane);
   }
 }
 
@@ -168,18 +177,21 @@ cudaError_t launch_batch_mt(const BatchQueue& q, Tile t, bool f32, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <int WPB, bool F32>
+template <int WPB, int OM>
 static cudaError_t launch_mt(const FillDesc& d, cudaStream_t s) {
   const uint64_t grid = (d.n_rows + WPB - 1) / WPB;
-  k_fill_mt<WPB, F32><<<(unsigned)grid, WPB * 32, 0, s>>>(d);
+  k_fill_mt<WPB, OM><<<(unsigned)grid, WPB * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_mt(const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
-  if (t.threads == 64) return d.f32 ? launch_mt<2, true>(d, s) : launch_mt<2, false>(d, s);
-  if (t.threads == 256) return d.f32 ? launch_mt<8, true>(d, s) : launch_mt<8, false>(d, s);
-  return d.f32 ? launch_mt<4, true>(d, s) : launch_mt<4, false>(d, s);
+  return with_mode(d.mode, [&](auto m) {
+    constexpr int OM = decltype(m)::value;
+    if (t.threads == 64) return launch_mt<2, OM>(d, s);
+    if (t.threads == 256) return launch_mt<8, OM>(d, s);
+    return launch_mt<4, OM>(d, s);
+  });
 }
 
 }  // namespace prng

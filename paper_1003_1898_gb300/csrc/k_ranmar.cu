@@ -24,9 +24,9 @@ __device__ __forceinline__ uint32_t ranmar_advance_c(uint32_t C0, uint32_t steps
   return c < 0 ? (uint32_t)(c + (int32_t)kRanmarM) : (uint32_t)c;
 }
 
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ uint32_t rm_conv(uint32_t x) {
-  if constexpr (F32) return __float_as_uint(__uint2float_rn(x) * 0x1p-24f);
+  if constexpr (OM == OUT_F32) return __float_as_uint(__uint2float_rn(x) * 0x1p-24f);
   else return x;
 }
 
@@ -47,7 +47,7 @@ constexpr int kRanmarRing = 132;
 // staging.  The state moves between HBM and the rings through one
 // cooperative pass of the block (eight consecutive streams per 32-byte
 // sector).
-template <int NW, bool F32, bool LIMITED>
+template <int NW, int OM, bool LIMITED>
 __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, int rows,
                                              uint32_t* smem) {
   constexpr int RS = kRanmarRing;
@@ -83,7 +83,18 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
     // mod 2^24.
     auto out_word = [&](uint32_t y, int s) {
       const uint32_t c = C - kd[s];
-      return rm_conv<F32>((y - c + (c >> 30)) & 0xFFFFFFu);
+      return rm_conv<OM>((y - c + (c >> 30)) & 0xFFFFFFu);
+    };
+    // Store of the step's 32 words (lanes with `on`); doubles pair lane l
+    // (even) with lane l + 1 (n is even, so a pair is never cut).
+    auto emit = [&](uint64_t col0, uint32_t v, bool on) {
+      const uint64_t col = col0 + l;
+      if constexpr (OM == OUT_F64) {
+        const uint32_t vb = __shfl_down_sync(0xFFFFFFFFu, v, 1);
+        if (on && !(l & 1) && (!LIMITED || rbase + col < d.limit)) st_pair<24>(orow + col, v, vb);
+      } else {
+        if (on && (!LIMITED || rbase + col < d.limit)) st_out(orow + col, v);
+      }
     };
     uint64_t g = 0;
     for (; g + 128 <= n; g += 128) {
@@ -92,10 +103,7 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
         const uint32_t y = rl[32 * s] - rl[32 * ((s + 2) & 3)];
         *wp[s] = y;
         __syncwarp();
-        if (store) {
-          const uint32_t v = out_word(y, s);
-          if (!LIMITED || rbase + g + 32 * s + l < d.limit) st_out(orow + g + 32 * s + l, v);
-        }
+        if (store) emit(g + 32 * s, out_word(y, s), true);
       }
       C = ranmar_advance_c(C, 128);
     }
@@ -111,10 +119,7 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
             *wp[s] = y;
           }
           __syncwarp();
-          if (on && store) {
-            const uint32_t v = out_word(y, s);
-            if (!LIMITED || rbase + g + 32 * s + l < d.limit) st_out(orow + g + 32 * s + l, v);
-          }
+          if (store) emit(g + 32 * s, on ? out_word(y, s) : 0u, on);
         }
       }
       C = ranmar_advance_c(C, (uint32_t)rem);
@@ -135,12 +140,12 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
   }
 }
 
-template <int T, bool F32>
+template <int T, int OM>
 __global__ void __launch_bounds__(T) k_fill_ranmar(const FillDesc d) {
   __shared__ uint32_t smem[(T / 32) * kRanmarRing];
   const uint64_t row0 = (uint64_t)blockIdx.x * (T / 32);
   const uint64_t left = d.n_rows - row0;
-  ranmar_warps<T / 32, F32, false>(d, row0, left < (uint64_t)(T / 32) ? (int)left : T / 32, smem);
+  ranmar_warps<T / 32, OM, false>(d, row0, left < (uint64_t)(T / 32) ? (int)left : T / 32, smem);
 }
 
 // Batched RANMAR fills: one block per item (up to T / 32 streams of one
@@ -150,7 +155,7 @@ template <int T, bool F32>
 __global__ void __launch_bounds__(T) k_batch_ranmar(const BatchQueue q) {
   __shared__ uint32_t smem[(T / 32) * kRanmarRing];
   const BatchItem si = q.items[blockIdx.x];
-  ranmar_warps<T / 32, F32, true>(q.reqs[si.req].d, si.row0, (int)si.rows, smem);
+  ranmar_warps<T / 32, F32 ? OUT_F32 : OUT_U32, true>(q.reqs[si.req].d, si.row0, (int)si.rows, smem);
 }
 
 template <int T, bool F32>
@@ -165,18 +170,20 @@ cudaError_t launch_batch_ranmar(const BatchQueue& q, Tile t, bool f32, cudaStrea
   return f32 ? launch_bm<256, true>(q, s) : launch_bm<256, false>(q, s);
 }
 
-template <int T, bool F32>
+template <int T, int OM>
 static cudaError_t launch_m(const FillDesc& d, cudaStream_t s) {
   const uint64_t grid = (d.n_rows + T / 32 - 1) / (T / 32);
   if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  k_fill_ranmar<T, F32><<<(unsigned)grid, T, 0, s>>>(d);
+  k_fill_ranmar<T, OM><<<(unsigned)grid, T, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_ranmar(const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
-  if (t.threads == 128) return d.f32 ? launch_m<128, true>(d, s) : launch_m<128, false>(d, s);
-  return d.f32 ? launch_m<256, true>(d, s) : launch_m<256, false>(d, s);
+  return with_mode(d.mode, [&](auto m) {
+    return t.threads == 128 ? launch_m<128, decltype(m)::value>(d, s)
+                            : launch_m<256, decltype(m)::value>(d, s);
+  });
 }
 
 }  // namespace prng

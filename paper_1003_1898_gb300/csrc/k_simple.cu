@@ -18,7 +18,7 @@
 namespace prng {
 
 struct GglGen {
-  static constexpr int SH = 7;
+  static constexpr int SH = 7, WB = 31;
   uint32_t x;
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) { x = st[row]; }
   __device__ __forceinline__ void store(uint32_t* st, uint64_t n, uint64_t row) const { st[row] = x; }
@@ -31,7 +31,7 @@ struct GglGen {
 };
 
 struct RanecuGen {
-  static constexpr int SH = 7;
+  static constexpr int SH = 7, WB = 31;
   uint32_t s1, s2;
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
     s1 = st[row];
@@ -55,7 +55,7 @@ struct RanecuGen {
 };
 
 struct Xor128Gen {
-  static constexpr int SH = 8;
+  static constexpr int SH = 8, WB = 32;
   uint32_t x, y, z, w;
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
     x = st[row];
@@ -81,10 +81,10 @@ struct Xor128Gen {
   }
 };
 
-template <class G, bool F32>
+template <class G, int OM>
 __device__ __forceinline__ uint32_t conv(uint32_t v) {
-  if constexpr (F32) return as_f32_bits<G::SH>(v);
-  else return v;
+  if constexpr (OM == OUT_F32) return as_f32_bits<G::SH>(v);
+  else return v;   // u32, or a raw draw paired at the copy-out
 }
 
 // Row-major tile, thread t's K staged draws in row t.  16-byte chunk ch of
@@ -96,7 +96,7 @@ __device__ __forceinline__ int swz(int row, int ch) { return ch ^ (row & 7); }
 
 // Streams [row0, row0 + T) of a fill, one per thread; smem holds S tiles of
 // T * K words.
-template <class G, int T, int K, int S, bool F32>
+template <class G, int T, int K, int S, int OM>
 __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
   static_assert(K % 32 == 0, "tile rows hold whole 8-chunk swizzle groups");
   constexpr int CH = K / 4;          // 16-byte chunks per row
@@ -132,14 +132,14 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
 #pragma unroll
       for (int c = 0; c < CH; c++) {
         uint4 v;
-        v.x = conv<G, F32>(g.next());
-        v.y = conv<G, F32>(g.next());
-        v.z = conv<G, F32>(g.next());
-        v.w = conv<G, F32>(g.next());
+        v.x = conv<G, OM>(g.next());
+        v.y = conv<G, OM>(g.next());
+        v.z = conv<G, OM>(g.next());
+        v.w = conv<G, OM>(g.next());
         *reinterpret_cast<uint4*>(my + 4 * (c ^ sw)) = v;
       }
     } else {
-      for (int c = 0; c < w; c++) my[4 * ((c >> 2) ^ sw) + (c & 3)] = conv<G, F32>(g.next());
+      for (int c = 0; c < w; c++) my[4 * ((c >> 2) ^ sw) + (c & 3)] = conv<G, OM>(g.next());
     }
     __syncthreads();
     if (w == K && vec_ok && last_row * d.pitch + c0 + K <= d.limit) {
@@ -148,7 +148,7 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
 #pragma unroll
       for (int k = 0; k < CH; k++)
         if (k < crows)
-          st_out4(dst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
+          st_chunk<OM, G::WB>(dst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
     } else {
       // Partial tile, unaligned output or a jump fill's last chunk: scalar
       // stores, warp per row, lanes on consecutive columns.
@@ -158,8 +158,15 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
         const uint64_t rr = row0 + r;
         if (rr >= d.n_rows) break;
         const uint64_t base = rr * d.pitch + c0;
-        for (int c = lane; c < w; c += 32)
-          if (base + c < d.limit) st_out(out + base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)]);
+        if constexpr (OM == OUT_F64) {   // w, base and the limit are even
+          for (int c = 2 * lane; c < w; c += 64)
+            if (base + c < d.limit)
+              st_pair<G::WB>(out + base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)],
+                             t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3) + 1]);
+        } else {
+          for (int c = lane; c < w; c += 32)
+            if (base + c < d.limit) st_out(out + base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)]);
+        }
       }
     }
     if constexpr (S == 1) __syncthreads();
@@ -168,10 +175,10 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
   if (active) g.store(d.state, d.n_rows, row);
 }
 
-template <class G, int T, int K, int S, bool F32>
+template <class G, int T, int K, int S, int OM>
 __global__ void __launch_bounds__(T) k_fill_simple(const FillDesc d) {
   extern __shared__ __align__(16) uint32_t smem[];
-  simple_rows<G, T, K, S, F32>(d, (uint64_t)blockIdx.x * T, smem);
+  simple_rows<G, T, K, S, OM>(d, (uint64_t)blockIdx.x * T, smem);
 }
 
 // Batched XOR128 fills: a block pops an item (T streams of one request).
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(T) k_batch_xor128(const BatchQueue q) {
     if (it >= q.n_items) break;
     const BatchItem si = q.items[it];
     const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
-    simple_rows<Xor128Gen, T, K, S, F32>(sd, si.row0, smem);
+    simple_rows<Xor128Gen, T, K, S, F32 ? OUT_F32 : OUT_U32>(sd, si.row0, smem);
   }
 }
 
@@ -229,24 +236,24 @@ __global__ void k_skip_step(const FillDesc d) {
   g.store(d.state, d.n_rows, row);
 }
 
-template <class G, int T, int K, int S, bool F32>
+template <class G, int T, int K, int S, int OM>
 static cudaError_t launch_tkf(const FillDesc& d, cudaStream_t s) {
   constexpr size_t bytes = (size_t)S * T * K * sizeof(uint32_t);
   static bool configured = false;  // attribute set once per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fill_simple<G, T, K, S, F32>,
+    cudaError_t e = cudaFuncSetAttribute(k_fill_simple<G, T, K, S, OM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const uint64_t grid = (d.n_rows + T - 1) / T;
-  k_fill_simple<G, T, K, S, F32><<<(unsigned)grid, T, bytes, s>>>(d);
+  k_fill_simple<G, T, K, S, OM><<<(unsigned)grid, T, bytes, s>>>(d);
   return cudaGetLastError();
 }
 
 template <class G, int T, int K, int S>
 static cudaError_t launch_tk(const FillDesc& d, cudaStream_t s) {
-  return d.f32 ? launch_tkf<G, T, K, S, true>(d, s) : launch_tkf<G, T, K, S, false>(d, s);
+  return with_mode(d.mode, [&](auto m) { return launch_tkf<G, T, K, S, decltype(m)::value>(d, s); });
 }
 
 // Supported tiles: (threads, cols, stages).

@@ -189,7 +189,7 @@ cudaError_t launch_jump_xor128(uint64_t x0, uint64_t n, uint32_t n_chunks, void*
     d.out = d_out;
     d.pitch = L;
     d.limit = n;
-    d.f32 = f32;
+    d.mode = f32 ? OUT_F32 : OUT_U32;
     e = launch_fill_simple(XOR128, d, default_tile(XOR128, 0), s);
   }
   const cudaError_t ef = cudaFreeAsync(S, s);

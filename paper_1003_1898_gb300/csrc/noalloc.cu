@@ -112,7 +112,7 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
     q.d.limit = (r.n_valid == 0 || r.n_valid > full) ? full : r.n_valid;
     q.d.pos = r.reseed ? initial_pos(st->gen) : st->pos;
     q.d.p = st->p;
-    q.d.f32 = r.f32 ? 1 : 0;
+    q.d.mode = r.f32 ? OUT_F32 : OUT_U32;
     q.seed = r.seed;
     q.gen = st->gen;
     q.reseed = r.reseed ? 1 : 0;

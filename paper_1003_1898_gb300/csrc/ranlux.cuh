@@ -150,15 +150,15 @@ __device__ __forceinline__ void rotate_fixed(uint32_t (&R)[24], const int s) {
 
 // Output of a word held as X = x * 2^8: x itself, or x * 2^-24 = X * 2^-32
 // (X has at most 24 significant bits, so the conversion is exact).
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ uint32_t lux_out(uint32_t X) {
-  if constexpr (F32) return __float_as_uint(__uint2float_rn(X) * 0x1p-32f);
+  if constexpr (OM == OUT_F32) return __float_as_uint(__uint2float_rn(X) * 0x1p-32f);
   else return X >> 8;
 }
 
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ uint32_t lux_conv(uint32_t x) {
-  if constexpr (F32) return __float_as_uint(__uint2float_rn(x) * 0x1p-24f);
+  if constexpr (OM == OUT_F32) return __float_as_uint(__uint2float_rn(x) * 0x1p-24f);
   else return x;
 }
 
@@ -174,7 +174,7 @@ __device__ __forceinline__ void discard_cycle(uint32_t (&R)[24], uint32_t& c) {
 
 // `cnt` SWB steps on a ring held in shared memory (ring[j], phase `ph`),
 // emitting each new word to out[k] when emit is set.
-template <bool F32>
+template <int OM>
 __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int cnt,
                                         uint32_t* out, bool emit) {
   for (int k = 0; k < cnt; k++) {
@@ -183,7 +183,7 @@ __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int
     c = (uint32_t)t >> 31;
     const uint32_t x = (uint32_t)t & 0xFFFFFFu;
     ring[ph] = x;
-    if (emit) out[k] = lux_conv<F32>(x);
+    if (emit) out[k] = lux_conv<OM>(x);
     ph = ph + 1 < 24 ? ph + 1 : 0;
   }
   return ph;
@@ -191,7 +191,7 @@ __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int
 
 // Streams [row0, row0 + T) of a fill, one per thread; smem holds a
 // row-major tile of T rows x SPW words (KT staged columns each).
-template <int T, int KT, int P, bool F32, bool LIMITED>
+template <int T, int KT, int P, int OM, bool LIMITED>
 __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
   static_assert(KT == 48, "the tile holds two blocks; its second half doubles as the scratch ring");
   constexpr int SPW = KT + 4;
@@ -201,7 +201,7 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   const uint64_t nr = d.n_rows;
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
-  RowFlusher<T, SPW, LIMITED> fl;
+  RowFlusher<T, SPW, LIMITED, OM, 24> fl;
   fl.init(smem, out, d.pitch, row0, nr, d.limit);
   uint32_t* my = smem + tid * SPW;            // this thread's tile row
   uint32_t* ring = my + 24;                   // scratch ring in columns 24..47
@@ -226,7 +226,7 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
     const int h = (int)((uint64_t)(24 - pos0) < n ? (uint64_t)(24 - pos0) : n);
     for (int jj = 0; jj < 24; jj++) ring[jj] = active ? d.state[jj * nr + row] : 0u;
     c = active ? d.state[24 * nr + row] : 0u;
-    const int ph = swb_smem<F32>(ring, 0, c, h, my, store);
+    const int ph = swb_smem<OM>(ring, 0, c, h, my, store);
     fill = h;
     j = h;
     if (j == n) {  // the fill ends inside the open block
@@ -259,8 +259,8 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
       uint4* dst = reinterpret_cast<uint4*>(my + fill);
 #pragma unroll
       for (int q = 0; q < 6; q++)
-        dst[q] = make_uint4(lux_out<F32>(R[4 * q]), lux_out<F32>(R[4 * q + 1]),
-                            lux_out<F32>(R[4 * q + 2]), lux_out<F32>(R[4 * q + 3]));
+        dst[q] = make_uint4(lux_out<OM>(R[4 * q]), lux_out<OM>(R[4 * q + 1]),
+                            lux_out<OM>(R[4 * q + 2]), lux_out<OM>(R[4 * q + 3]));
     }
     fill += 24;
     j += 24;
@@ -273,7 +273,7 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
     if (fill > 0) flush();
 #pragma unroll
     for (int jj = 0; jj < 24; jj++) ring[jj] = R[jj] >> 8;
-    const int ph = swb_smem<F32>(ring, 0, c, m, my, store);
+    const int ph = swb_smem<OM>(ring, 0, c, m, my, store);
     fill = m;
     if (active) {
       for (int jj = 0; jj < 24; jj++) {
@@ -294,10 +294,10 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   }
 }
 
-template <int T, int KT, int P, bool F32>
+template <int T, int KT, int P, int OM>
 __global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
   extern __shared__ uint32_t smem[];
-  ranlux_rows<T, KT, P, F32, false>(d, (uint64_t)blockIdx.x * T, smem);
+  ranlux_rows<T, KT, P, OM, false>(d, (uint64_t)blockIdx.x * T, smem);
 }
 
 // Batched RANLUX fills of luxury P: a block pops an item (T streams).
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_batch_ranlux(const BatchQueue q)
     if (it >= q.n_items) break;
     const BatchItem si = q.items[it];
     const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
-    ranlux_rows<T, KT, P, F32, true>(sd, si.row0, smem);
+    ranlux_rows<T, KT, P, F32 ? OUT_F32 : OUT_U32, true>(sd, si.row0, smem);
   }
 }
 
@@ -331,18 +331,18 @@ static cudaError_t launch_bl(const BatchQueue& q, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int T, int KT, int P, bool F32>
+template <int T, int KT, int P, int OM>
 static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
   constexpr size_t bytes = (size_t)T * (KT + 4) * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fill_ranlux<T, KT, P, F32>,
+    cudaError_t e = cudaFuncSetAttribute(k_fill_ranlux<T, KT, P, OM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const uint64_t grid = (d.n_rows + T - 1) / T;
-  k_fill_ranlux<T, KT, P, F32><<<(unsigned)grid, T, bytes, s>>>(d);
+  k_fill_ranlux<T, KT, P, OM><<<(unsigned)grid, T, bytes, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -350,9 +350,12 @@ static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
 // k_ranlux_p<P>.cu, so that the luxury levels compile in parallel).
 template <int P>
 cudaError_t ranlux_fill_p(const FillDesc& d, Tile t, cudaStream_t s) {
-  if (t.threads == 64) return d.f32 ? launch_l<64, 48, P, true>(d, s) : launch_l<64, 48, P, false>(d, s);
-  if (t.threads == 256) return d.f32 ? launch_l<256, 48, P, true>(d, s) : launch_l<256, 48, P, false>(d, s);
-  return d.f32 ? launch_l<128, 48, P, true>(d, s) : launch_l<128, 48, P, false>(d, s);
+  return with_mode(d.mode, [&](auto m) {
+    constexpr int OM = decltype(m)::value;
+    if (t.threads == 64) return launch_l<64, 48, P, OM>(d, s);
+    if (t.threads == 256) return launch_l<256, 48, P, OM>(d, s);
+    return launch_l<128, 48, P, OM>(d, s);
+  });
 }
 
 template <int P>

@@ -335,3 +335,103 @@ def test_jump_full_size_sampled(gen):
     if gen == "ggl":
         assert int(got[np.searchsorted(pos, 9999)]) == 1043618065
     del out
+
+
+# ------------------------------------------------------------ doubles from pairs
+
+def fill_f64(h, n_streams, n_per, offset=0):
+    buf = torch.full((n_streams * n_per + offset + 2,), -7.0, dtype=torch.float64, device="cuda")
+    view = buf[offset:offset + n_streams * n_per]
+    P.prng_fill_f64(h, view.data_ptr(), n_per)
+    torch.cuda.synchronize()
+    assert torch.all(buf[offset + n_streams * n_per:] == -7.0), "write past the end"
+    assert torch.all(buf[:offset] == -7.0), "write before the start"
+    return view.reshape(n_streams, n_per).cpu().numpy()
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+@pytest.mark.parametrize("ns,nper", [(1, 1), (130, 333), (257, 1000), (33, 4096)])
+def test_f64_every_element(gen, ns, nper):
+    lux = lux_of(gen, 223)
+    ref = oracle.fill_f64(gen, 21, ns, nper, luxury=lux)
+    h = P.prng_create(gen, 21, ns, lux)
+    try:
+        got = fill_f64(h, ns, nper)
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("gen", inputs.GENS)
+def test_f64_continues_u32_and_f32_fills(gen):
+    # u32 (even count), f64, f32, f64 on one handle = the oracle stream cut there.
+    lux = lux_of(gen, 97)
+    ns = 70
+    h = P.prng_create(gen, 8, ns, lux)
+    try:
+        a = u32(fill(h, ns, 50))
+        b = fill_f64(h, ns, 61)
+        c = fill(h, ns, 30, "f32").cpu().numpy()
+        d = fill_f64(h, ns, 700, offset=1)          # 8- but not 16-byte aligned
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(a, oracle.fill(gen, 8, ns, 50, luxury=lux))
+    np.testing.assert_array_equal(b.view(np.uint64),
+                                  oracle.fill_f64(gen, 8, ns, 61, luxury=lux, skip=50).view(np.uint64))
+    _, cf = oracle.fill(gen, 8, ns, 30, luxury=lux, skip=172, want_f32=True)
+    np.testing.assert_array_equal(c.view(np.uint32), cf.view(np.uint32))
+    np.testing.assert_array_equal(d.view(np.uint64),
+                                  oracle.fill_f64(gen, 8, ns, 700, luxury=lux, skip=202).view(np.uint64))
+
+
+@pytest.mark.parametrize("gen", ["ranlux", "mt19937"])
+def test_f64_needs_even_position(gen):
+    lux = lux_of(gen, 24)
+    h = P.prng_create(gen, 5, 40, lux)
+    try:
+        fill(h, 40, 7)                                   # odd count: odd position
+        out = torch.full((40 * 10,), -7.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(P.PrngError) as err:
+            P.prng_fill_f64(h, out.data_ptr(), 10)
+        assert err.value.code == -11
+        torch.cuda.synchronize()
+        assert torch.all(out == -7.0)
+        P.prng_skip(h, 1)
+        got = fill_f64(h, 40, 10)
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got.view(np.uint64),
+                                  oracle.fill_f64(gen, 5, 40, 10, luxury=lux, skip=8).view(np.uint64))
+
+
+@pytest.mark.parametrize("p", inputs.LUXURY_LEVELS)
+def test_f64_ranlux_levels_from_even_positions(p):
+    ns = 65
+    h = P.prng_create("ranlux", 31, ns, p)
+    try:
+        fill(h, ns, 10)                                  # position 10 of the first block
+        got = fill_f64(h, ns, 101)
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got.view(np.uint64),
+                                  oracle.fill_f64("ranlux", 31, ns, 101, luxury=p, skip=10).view(np.uint64))
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranmar", "mt19937"])
+def test_f64_full_size_sampled(gen):
+    ns, nper = (inputs.ROOFLINE_MT["n_streams"], inputs.ROOFLINE_MT["n_per"] // 2) if gen == "mt19937" \
+        else (inputs.ROOFLINE["n_streams"], inputs.ROOFLINE["n_per"] // 2)
+    h = P.prng_create(gen, inputs.SEED_BASE, ns, 0)
+    try:
+        out = torch.empty((ns, nper), dtype=torch.float64, device="cuda")
+        P.prng_fill_f64(h, out.data_ptr(), nper)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(ns, 6)
+        got = out[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        for i, r in enumerate(rows):
+            ref = oracle.fill_f64(gen, inputs.SEED_BASE, 1, nper, stream0=int(r))[0]
+            np.testing.assert_array_equal(got[i].view(np.uint64), ref.view(np.uint64), err_msg=f"row {r}")
+        assert float(out.min()) >= 0.0 and float(out.max()) < 1.0
+    finally:
+        P.prng_destroy(h)
+        del out
