@@ -74,6 +74,12 @@ def lib():
             L.orc_ggl_jump.argtypes = [u32, u64]
             L.orc_xor128_jump.restype = None
             L.orc_xor128_jump.argtypes = [vp, u64]
+            L.orc_mt_jump.restype = None
+            L.orc_mt_jump.argtypes = [vp, u64]
+            L.orc_mt_charpoly_info.restype = i32
+            L.orc_mt_charpoly_info.argtypes = [ctypes.POINTER(i32)]
+            L.orc_mt_next.restype = u32
+            L.orc_mt_next.argtypes = [vp]
             L.orc_serial_sample.restype = ctypes.c_int
             L.orc_serial_sample.argtypes = [i32, u64, vp, u64, vp]
             L.orc_serial_fill.restype = ctypes.c_int
@@ -193,6 +199,47 @@ def xor128_jump(state, k: int):
     s = np.ascontiguousarray(np.asarray(state, dtype=np.uint32).copy())
     lib().orc_xor128_jump(s.ctypes.data, k & (2**64 - 1))
     return s
+
+
+def mt_jump(table, mti: int, k: int):
+    """MT19937 table (624 words) k outputs later (mti unchanged)."""
+    class _Mt(ctypes.Structure):
+        _fields_ = [("mt", ctypes.c_uint32 * 624), ("mti", ctypes.c_int32)]
+    s = _Mt()
+    s.mt[:] = [int(x) for x in table]
+    s.mti = mti
+    lib().orc_mt_jump(ctypes.byref(s), k & (2**64 - 1))
+    return np.array(s.mt[:], dtype=np.uint32)
+
+
+def mt_charpoly_info():
+    """(degree, number of terms) of MT19937's characteristic polynomial."""
+    n = ctypes.c_int32()
+    d = lib().orc_mt_charpoly_info(ctypes.byref(n))
+    return int(d), int(n.value)
+
+
+def mt_init_table(seed: int):
+    """init_genrand's table for a 32-bit seed (Section 3.7 initialisation)."""
+    t = [seed & 0xFFFFFFFF]
+    for i in range(1, 624):
+        t.append((1812433253 * (t[-1] ^ (t[-1] >> 30)) + i) & 0xFFFFFFFF)
+    return np.array(t, dtype=np.uint32)
+
+
+def mt_draws_from(table, mti: int, n: int, with_state: bool = False):
+    """n outputs of MT19937 from an explicit (table, mti) state (and, with
+    with_state, the (table, mti) state after them)."""
+    class _Mt(ctypes.Structure):
+        _fields_ = [("mt", ctypes.c_uint32 * 624), ("mti", ctypes.c_int32)]
+    s = _Mt()
+    s.mt[:] = [int(x) for x in table]
+    s.mti = mti
+    L = lib()
+    out = np.array([L.orc_mt_next(ctypes.byref(s)) for _ in range(n)], dtype=np.uint32)
+    if with_state:
+        return out, np.array(s.mt[:], dtype=np.uint32), int(s.mti)
+    return out
 
 
 def serial_sample(gen, x0: int, positions):

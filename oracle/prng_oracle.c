@@ -36,6 +36,7 @@
 
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* ---------------------------------------------------------------- seeding */
@@ -522,6 +523,115 @@ static void orc_xor128_from_s(orc_xor128 *x, uint64_t s) {
   orc_xor128_init(x, lo, hi, z, w);
 }
 
+/* MT19937 jump-ahead over GF(2).  The table of 624 words is a window
+ * (w_s, ..., w_{s+623}) of the word sequence of Appendix A, "Mersenne
+ * twister" (w_{t+624} = w_{t+397} ^ (w_t^upper | w_{t+1}^lower) A), the
+ * next outputs being tempered words of it, so k outputs later the table is
+ * the window k words on (the read index mti is unchanged).  Moving the window
+ * by one word is a linear map T over GF(2).  Its characteristic polynomial
+ * phi, of degree 19937, is found here by the Berlekamp-Massey algorithm from
+ * 2 x 19937 output bits, and on the state T^k acts as g(T) with g = t^k mod
+ * phi.  T drops the low 31 bits of the window's oldest word, which are not
+ * part of the state, so the window is moved by g(T) for t^(k-1) and then
+ * one more word: word j of the new table is the XOR of w_{1+i+j} over the
+ * coefficients g_i = 1. */
+#define ORC_MT_DEG 19937
+static uint8_t *orc_mt_phi;            /* coefficients of t^0 .. t^19937 */
+static int32_t orc_mt_phi_exp[ORC_MT_DEG + 1];
+static int32_t orc_mt_phi_nterms;
+
+static void orc_mt_charpoly(void) {
+  if (orc_mt_phi) return;
+  const int32_t N = 2 * ORC_MT_DEG;
+  uint8_t *seq = (uint8_t *)malloc(N), *C = (uint8_t *)calloc(N + 1, 1);
+  uint8_t *B = (uint8_t *)calloc(N + 1, 1), *T = (uint8_t *)malloc(N + 1);
+  orc_mt st;
+  orc_mt_init(&st, 5489u);
+  for (int32_t n = 0; n < N; n++) seq[n] = (uint8_t)(orc_mt_next(&st) & 1u);
+  /* Berlekamp-Massey: the shortest C with sum_{i=0..L} C_i s_{n-i} = 0. */
+  int32_t L = 0, m = 1;
+  C[0] = B[0] = 1;
+  for (int32_t n = 0; n < N; n++) {
+    uint8_t d = seq[n];
+    for (int32_t i = 1; i <= L; i++) d ^= (uint8_t)(C[i] & seq[n - i]);
+    if (!d) {
+      m++;
+      continue;
+    }
+    if (2 * L <= n) {
+      memcpy(T, C, (size_t)N + 1);
+      for (int32_t i = 0; i + m <= N; i++) C[i + m] ^= B[i];
+      L = n + 1 - L;
+      memcpy(B, T, (size_t)N + 1);
+      m = 1;
+    } else {
+      for (int32_t i = 0; i + m <= N; i++) C[i + m] ^= B[i];
+      m++;
+    }
+  }
+  /* phi(t) = t^L C(1/t). */
+  uint8_t *phi = (uint8_t *)calloc((size_t)L + 1, 1);
+  for (int32_t i = 0; i <= L; i++) phi[L - i] = C[i];
+  orc_mt_phi_nterms = 0;
+  for (int32_t e = 0; e <= L; e++)
+    if (phi[e]) orc_mt_phi_exp[orc_mt_phi_nterms++] = e;
+  free(seq); free(C); free(B); free(T);
+  orc_mt_phi = phi;
+}
+
+/* Degree and number of terms of the characteristic polynomial. */
+int32_t orc_mt_charpoly_info(int32_t *n_terms) {
+  orc_mt_charpoly();
+  if (n_terms) *n_terms = orc_mt_phi_nterms;
+  return orc_mt_phi_exp[orc_mt_phi_nterms - 1];
+}
+
+/* r (coefficients 0 .. 2 D - 2) reduced mod phi in place. */
+static void orc_mt_reduce(uint8_t *r, int32_t top) {
+  for (int32_t p = top; p >= ORC_MT_DEG; p--) {
+    if (!r[p]) continue;
+    for (int32_t j = 0; j < orc_mt_phi_nterms; j++) r[p - ORC_MT_DEG + orc_mt_phi_exp[j]] ^= 1;
+  }
+}
+
+void orc_mt_jump(orc_mt *s, uint64_t k) {
+  if (k == 0) return;
+  orc_mt_charpoly();
+  const int32_t D = ORC_MT_DEG;
+  uint8_t *g = (uint8_t *)calloc(2 * (size_t)D, 1), *r = (uint8_t *)calloc(2 * (size_t)D, 1);
+  /* g = t^(k-1) mod phi, left to right over the bits of k - 1. */
+  const uint64_t e = k - 1;
+  g[0] = 1;
+  for (int b = 63; b >= 0; b--) {
+    memset(r, 0, 2 * (size_t)D);
+    for (int32_t i = 0; i < D; i++) r[2 * i] = g[i];          /* squaring over GF(2) */
+    orc_mt_reduce(r, 2 * D - 2);
+    if ((e >> b) & 1u) {                                      /* times t */
+      memmove(r + 1, r, (size_t)D);
+      r[0] = 0;
+      orc_mt_reduce(r, D);
+    }
+    memcpy(g, r, (size_t)D);
+  }
+  /* The word sequence from the table, then the new table. */
+  const int32_t W = D + 624 + 1;
+  uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)W);
+  for (int32_t j = 0; j < 624; j++) w[j] = s->mt[j];
+  for (int32_t t = 0; t + 624 < W; t++) {
+    uint32_t y = (w[t] & 0x80000000u) | (w[t + 1] & 0x7FFFFFFFu);
+    uint32_t ya = y >> 1;
+    if (y & 1u) ya ^= 0x9908B0DFu;
+    w[t + 624] = w[t + 397] ^ ya;
+  }
+  for (int32_t j = 0; j < 624; j++) {
+    uint32_t acc = 0;
+    for (int32_t i = 0; i < D; i++)
+      if (g[i]) acc ^= w[1 + i + j];
+    s->mt[j] = acc;
+  }
+  free(w); free(g); free(r);
+}
+
 static int orc_serial_start(orc_stream *st, int32_t gen, uint64_t x0) {
   memset(st, 0, sizeof(*st));
   st->gen = gen;
@@ -538,6 +648,11 @@ static int orc_serial_start(orc_stream *st, int32_t gen, uint64_t x0) {
   }
   if (gen == ORC_XOR128) {
     orc_xor128_from_s(&st->s.x, x0);
+    return 0;
+  }
+  if (gen == ORC_MT19937) {
+    if (x0 > 0xFFFFFFFFull) return -1;
+    orc_mt_init(&st->s.t, (uint32_t)x0);
     return 0;
   }
   return -1;

@@ -120,10 +120,18 @@ void orc_ranecu_jump(orc_ranecu *s, uint64_t k);
 /* XOR128 jump-ahead: the state after k steps, T^k v over GF(2) with T the
  * 128 x 128 matrix of one step (Appendix A, "XORShift", matrix form). */
 void orc_xor128_jump(orc_xor128 *s, uint64_t k);
+/* MT19937 jump-ahead: the state k outputs later (the table moved k words on
+ * along the word sequence, mti unchanged), by g(T) with g = t^(k-1) mod phi
+ * and one more step; phi, the characteristic polynomial of the one-word
+ * step T, comes from Berlekamp-Massey on 2 x 19937 output bits. */
+void orc_mt_jump(orc_mt *s, uint64_t k);
+/* Degree of phi; *n_terms receives its number of nonzero coefficients. */
+int32_t orc_mt_charpoly_info(int32_t *n_terms);
 
 /* The single serial sequence started at x0 (GGL: x0 = seed value; RANECU:
  * x0 = s1 | s2 << 32; XOR128: the state the stream seeding map gives for the
- * per-stream value s = x0): out[j] = draw j+1.  Returns the draws at sorted
+ * per-stream value s = x0; MT19937: init_genrand(x0), x0 < 2^32):
+ * out[j] = draw j+1.  Returns the draws at sorted
  * 0-based positions pos[0..n_pos) by stepping serially. */
 int orc_serial_sample(int32_t gen, uint64_t x0, const uint64_t *pos,
                       uint64_t n_pos, uint32_t *out_u32);

@@ -234,6 +234,44 @@ def test_xor128_gf2_linearity():
         np.testing.assert_array_equal(sab, sa ^ sb)
 
 
+# ---------------------------------------------------------------- MT19937 jump-ahead
+
+def test_mt_characteristic_polynomial():
+    # MT19937's characteristic polynomial has degree 19937 (the period
+    # exponent, Section 3.7) and 135 nonzero terms (Matsumoto and Nishimura
+    # 1998); the oracle finds it by Berlekamp-Massey from the output bits.
+    assert oracle.mt_charpoly_info() == (19937, 135)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 227, 397, 623, 624, 625, 1248, 19937, 100003])
+@pytest.mark.parametrize("drawn", [0, 624, 311, 1000])
+def test_mt_jump_equals_stepping(k, drawn):
+    # Brute force: from the state after `drawn` outputs (a fresh table, a
+    # table just used up, or one read part-way), the outputs after a jump of
+    # k are outputs k+1, k+2, ... of the unjumped state.
+    table = oracle.mt_init_table(5489 + drawn)
+    _, tab, mti = oracle.mt_draws_from(table, 624, drawn, with_state=True)
+    serial = oracle.mt_draws_from(tab, mti, k + 40)
+    jumped = oracle.mt_jump(tab, mti, k)
+    np.testing.assert_array_equal(oracle.mt_draws_from(jumped, mti, 40), serial[k:k + 40])
+
+
+def test_mt_jump_composes():
+    # T^a T^b = T^(a+b) for large a, b (beyond brute force).
+    table = oracle.mt_init_table(4357)
+    a, b = 2**40 + 12345, 2**33 + 7
+    one = oracle.mt_jump(oracle.mt_jump(table, 624, a), 624, b)
+    both = oracle.mt_jump(table, 624, a + b)
+    np.testing.assert_array_equal(one, both)
+
+
+def test_mt_serial_start_is_init_genrand():
+    # The single-sequence MT19937 fill starts from init_genrand(x0): draw
+    # 10000 from x0 = 5489 is the published check value.
+    out = oracle.serial_fill("mt19937", 5489, 10000)
+    assert int(out[9999]) == 4123659995
+
+
 # ---------------------------------------------------------------- doubles from pairs
 
 F64_RULE = {"ranmar": (0, 0, 24, 48), "ranlux": (0, 0, 24, 48),
