@@ -284,6 +284,21 @@ def measure_xor128_jump(P, torch, out_u, h_xor, stream):
             "skip_2p40": {"streams": N_STREAMS, "ms": skip_ms}}
 
 
+def measure_mt_jump(P, torch, out_u, h_mt, stream):
+    """MT19937 jump-ahead over GF(2): prng_skip(2^40) of the 8,192-stream
+    handle (the jump polynomial applied to every table), and the
+    single-sequence fill of 2^30 draws from init_genrand(5489) in 8,192
+    chunks (chunk starts by doubling passes, then the ordinary fill)."""
+    sid = stream.cuda_stream
+    skip_ms = _time_ms(torch, stream, lambda: P.prng_skip(h_mt, 2**40, sid), reps=3, warm=1)
+    ms = _time_ms(torch, stream, lambda: P.prng_fill_jump_u32("mt19937", 5489, JUMP_N, MT_STREAMS,
+                                                               out_u.data_ptr(), sid), reps=3, warm=1)
+    return {"skip_2p40": {"streams": MT_STREAMS, "ms": skip_ms},
+            "fill": {"numbers": JUMP_N, "chunks": MT_STREAMS, "ms": ms,
+                     "numbers_per_s": JUMP_N / (ms / 1e3),
+                     "frac_hbm": 4 * JUMP_N / (ms / 1e3) / 1e9 / peaks()[0]}}
+
+
 def measure_f64(P, torch, out_u, handles, seed_r, stream):
     """Doubles from pairs of draws: 2^29 doubles (4 GiB) per generator on
     the roofline handles, each double made of two draws; bytes per launch
@@ -449,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
     lux_sweep = measure_luxury_sweep(P, torch, dev, stream, clk.summary().get("sm_mhz"))
     xor128_jump = measure_xor128_jump(P, torch, out_u, handles["xor128"], stream)
     f64 = measure_f64(P, torch, out_u, handles, seed_r, stream)
+    mt_jump = measure_mt_jump(P, torch, out_u, handles["mt19937"], stream)
 
     # Batched requests (20,000 mixed fills): one graph launch vs one plain
     # re-seed + fill per request.
@@ -506,6 +522,7 @@ def run_ours(args, rank, world, local_rank):
         "luxury_sweep": lux_sweep,
         "xor128_jump": xor128_jump,
         "f64": f64,
+        "mt_jump": mt_jump,
         "tiles": {"tuned_cache": bool(tuned),
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }

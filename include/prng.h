@@ -109,7 +109,13 @@ int prng_fill_f64(prng_state *st, double *d_out, uint64_t n_per_stream, void *st
  * fill of k whose output is thrown away).  GGL and RANECU jump in O(log k)
  * by a^k mod m (Appendix A, eq. MLCG); XOR128 (k >= 256) by T^k, the k-th
  * power of its 128 x 128 step matrix over GF(2) (Appendix A, "XORShift",
- * matrix form), formed on the host in O(log k); the others step. */
+ * matrix form), formed on the host in O(log k); MT19937 (k >= 2^20) by the
+ * jump polynomial t^(k-1) mod phi (phi the degree-19937 characteristic
+ * polynomial of one word step, Section 3.7) and one more step, each table
+ * moving k words along its word sequence (about 6 million word XORs per
+ * stream, whatever k; the read index is unchanged, so a later state blob
+ * differs from a stepped one's in layout, not in the draws); the others
+ * step. */
 int prng_skip(prng_state *st, uint64_t k, void *stream);
 
 /* Checkpoint.  prng_get_state copies the handle's full state into h_buf
@@ -122,7 +128,7 @@ int prng_skip(prng_state *st, uint64_t k, void *stream);
 int prng_get_state(prng_state *st, void *h_buf, size_t *bytes);
 int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
 
-/* Single-sequence jump-ahead fill (GGL, RANECU and XOR128): write draws
+/* Single-sequence jump-ahead fill (GGL, RANECU, XOR128 and MT19937): write draws
  * 1..n of the one sequence started at x0 to d_out[0..n), computed as
  * n_chunks contiguous chunks in parallel, L = ceil(n / n_chunks) draws each.
  * GGL: x0 in [1, 2^31-2], chunk c starts from a^(c*L) x0 mod m by
@@ -135,7 +141,11 @@ int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
  * sequence into more, shorter chunks than asked (at least 131072 when n
  * allows 64 draws each; the output is the same), and allocates a
  * stream-ordered scratch array of 16 bytes per chunk (PRNG_EALLOC if that
- * fails).  Other generators return PRNG_EUNSUPPORTED. */
+ * fails).  MT19937: x0 < 2^32, the sequence of init_genrand(x0); chunk c
+ * starts from its table moved c*L words on, built in log2(n_chunks)
+ * doubling passes of the jump polynomial (about 6 million word XORs per
+ * chunk, so a few thousand chunks is the useful range), with a scratch
+ * array of 2.5 KB per chunk.  Other generators return PRNG_EUNSUPPORTED. */
 int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        uint32_t *d_out, void *stream);
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,

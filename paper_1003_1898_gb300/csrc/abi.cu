@@ -64,13 +64,16 @@ int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int mode, cudaStream_
 int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
               cudaStream_t s) {
   if (gen < 0 || gen > 5) return PRNG_EGEN;
-  if (gen != GGL && gen != RANECU && gen != XOR128) return PRNG_EUNSUPPORTED;
+  if (gen != GGL && gen != RANECU && gen != XOR128 && gen != MT19937) return PRNG_EUNSUPPORTED;
   if (n == 0) return PRNG_OK;
   if (d_out == nullptr) return PRNG_ENULL;
   if (n_chunks == 0) return PRNG_ESIZE;
   if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
-  if (gen == XOR128) {  // every 64-bit x0 is a valid seeding value
-    const cudaError_t e = launch_jump_xor128(x0, n, n_chunks, d_out, f32, s);
+  if (gen == XOR128 || gen == MT19937) {
+    if (gen == MT19937 && x0 > 0xFFFFFFFFull) return PRNG_ESEED;
+    const cudaError_t e = gen == XOR128 ? launch_jump_xor128(x0, n, n_chunks, d_out, f32, s)
+                                        : launch_jump_mt(x0, n, n_chunks, d_out,
+                                                         f32 ? OUT_F32 : OUT_U32, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? PRNG_EALLOC : PRNG_ECUDA;
@@ -213,6 +216,9 @@ int prng_fill_f64(prng_state* st, double* d_out, uint64_t n_per_stream, void* st
 // XOR128 skips of at least this many steps use the GF(2) matrix power
 // (about 128 column XORs per stream) instead of stepping.
 constexpr uint64_t kXor128MatrixSkip = 256;
+// MT19937 skips of at least this many outputs use the polynomial jump (about
+// 19937 x 312 word XORs per stream) instead of stepping.
+constexpr uint64_t kMtPolySkip = 1ull << 20;
 
 int prng_skip(prng_state* st, uint64_t k, void* stream) {
   if (st == nullptr) return PRNG_ENULL;
@@ -223,6 +229,10 @@ int prng_skip(prng_state* st, uint64_t k, void* stream) {
     e = launch_skip_mlcg(st->gen, st->d_state, st->n_streams, k, s);
   } else if (st->gen == XOR128 && k >= kXor128MatrixSkip) {
     e = launch_skip_xor128(st->d_state, st->n_streams, k, s);
+  } else if (st->gen == MT19937 && k >= kMtPolySkip) {
+    // The tables move k words along the sequence; the read index stays.
+    if (launch_skip_mt(st->d_state, st->n_streams, k, s) != cudaSuccess) return PRNG_ECUDA;
+    return PRNG_OK;
   } else {
     FillDesc d{};
     d.state = st->d_state;

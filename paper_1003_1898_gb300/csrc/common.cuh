@@ -88,6 +88,19 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// MT19937 jump-ahead over GF(2): a polynomial g of degree < 19937 over GF(2)
+// (bit i of word i / 32 is the coefficient of t^i) applied to tables of
+// 624 words; prng_skip of k outputs on a handle's tables ([n][624]); the
+// single-sequence chunked fill from init_genrand(x0).
+struct MtPoly {
+  uint32_t w[624];
+};
+cudaError_t launch_mt_poly_apply(const MtPoly& g, uint32_t* state, uint64_t r0, uint64_t r1,
+                                 uint64_t src_off, cudaStream_t s);
+cudaError_t launch_skip_mt(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s);
+cudaError_t launch_jump_mt(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int mode,
+                           cudaStream_t s);
+
 // XOR128 jump-ahead over GF(2): prng_skip of k steps on a handle's state
 // (struct-of-arrays [4][n]), and the single-sequence chunked fill.
 cudaError_t launch_skip_xor128(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s);

@@ -20,7 +20,8 @@ ROOFLINE_MT = dict(n_streams=8192, n_per=131072)        # MT19937: 624-word tabl
 LUX_SWEEP = dict(n_streams=65536, n_per=4096)           # 2^28 draws per luxury level
 JUMP = dict(n=2**30, n_chunks=65536)                    # single sequence from x0 = 1
 JUMP_X0 = {"ggl": 1, "ranecu": 1 | (1 << 32),          # RANECU: s1 = s2 = 1
-           "xor128": SEED_BASE}                          # XOR128: seeding value s = x0
+           "xor128": SEED_BASE,                          # XOR128: seeding value s = x0
+           "mt19937": 5489}                              # MT19937: init_genrand(5489)
 
 # Batched requests: draws per stream a request is split into.
 DRAWS_PER_STREAM = {"mt19937": 65536, "ranmar": 16384}

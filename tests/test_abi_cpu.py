@@ -49,8 +49,9 @@ def test_create_rejects_bad_arguments(L):
 
 def test_jump_rejects_bad_arguments(L):
     buf = ctypes.c_void_p(16)  # never dereferenced: validation fails first
-    assert L.prng_fill_jump_u32(P.MT19937, 1, 10, 1, buf, None) == -7
     assert L.prng_fill_jump_u32(P.RANMAR, 1, 10, 1, buf, None) == -7
+    assert L.prng_fill_jump_u32(P.RANLUX, 1, 10, 1, buf, None) == -7
+    assert L.prng_fill_jump_u32(P.MT19937, 2**32, 10, 1, buf, None) == -9    # MT: 32-bit seed
     assert L.prng_fill_jump_u32(P.XOR128, 1, 10, 0, buf, None) == -3      # XOR128: no chunks
     assert L.prng_fill_jump_u32(P.XOR128, 1, 10, 1, None, None) == -4
     assert L.prng_fill_jump_u32(9, 1, 10, 1, buf, None) == -1

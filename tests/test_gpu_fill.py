@@ -166,6 +166,32 @@ def test_xor128_skip_by_matrix_power(k):
                                       err_msg=f"stream {i}")
 
 
+def _mt_seeded_table(seed, i):
+    # Reading R1 for MT19937: init_genrand(lo32(splitmix64(seed + i))).
+    return oracle.mt_init_table(oracle.splitmix64(seed + i) & 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("k", [2**20, 2**20 + 1, 10**7 + 3, 2**40 + 7])
+@pytest.mark.parametrize("first", [0, 1000])
+def test_mt_skip_by_polynomial(k, first):
+    # Skips of 2^20 or more move every table k words on by the jump
+    # polynomial; checked against the oracle's own jump of each stream's
+    # state (after `first` outputs, so from inside a table too).
+    ns, nper = 24, 700
+    h = P.prng_create("mt19937", 13, ns, 0)
+    try:
+        if first:
+            fill(h, ns, first)
+        P.prng_skip(h, k)
+        got = u32(fill(h, ns, nper))
+    finally:
+        P.prng_destroy(h)
+    for i in range(ns):
+        _, tab, mti = oracle.mt_draws_from(_mt_seeded_table(13, i), 624, first, with_state=True)
+        want = oracle.mt_draws_from(oracle.mt_jump(tab, mti, k), mti, nper)
+        np.testing.assert_array_equal(got[i], want, err_msg=f"stream {i}")
+
+
 def test_xor128_skip_matrix_equals_stepping():
     # The same skip on the two sides of the switch: 300 = 255 + 45 steps.
     ns, nper = 129, 20
@@ -244,8 +270,8 @@ def test_zero_length_fill_is_noop():
 
 # ------------------------------------------------------------ jump-ahead
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
-@pytest.mark.parametrize("n,chunks", [(1, 1), (1000, 7), (100003, 37), (65536, 65536), (50000, 1)])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
+@pytest.mark.parametrize("n,chunks", [(1, 1), (1000, 7), (100003, 37), (65536, 512), (50000, 1)])
 def test_jump_fill_small_every_element(gen, n, chunks):
     x0 = inputs.JUMP_X0[gen]
     ref = oracle.serial_fill(gen, x0, n)
@@ -261,9 +287,9 @@ def test_jump_fill_small_every_element(gen, n, chunks):
                                   oracle.to_f32(gen, ref).view(np.uint32))
 
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
 def test_jump_fill_other_start(gen):
-    x0 = {"ggl": 123456789, "ranecu": 987654 | (13579 << 32), "xor128": 0}[gen]
+    x0 = {"ggl": 123456789, "ranecu": 987654 | (13579 << 32), "xor128": 0, "mt19937": 4357}[gen]
     n = 77777
     out = torch.empty((n,), dtype=torch.int32, device="cuda")
     P.prng_fill_jump_u32(gen, x0, n, 100, out.data_ptr())
@@ -321,9 +347,11 @@ def test_luxury_sweep_config_sampled(p):
     _sampled_rows_check("ranlux", p, cfg["n_streams"], cfg["n_per"], 8, "f32")
 
 
-@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128"])
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
 def test_jump_full_size_sampled(gen):
     n, chunks = inputs.JUMP["n"], inputs.JUMP["n_chunks"]
+    if gen == "mt19937":
+        chunks = inputs.ROOFLINE_MT["n_streams"]     # one warp per chunk, as the bulk fill
     x0 = inputs.JUMP_X0[gen]
     out = torch.empty((n,), dtype=torch.int32, device="cuda")
     P.prng_fill_jump_u32(gen, x0, n, chunks, out.data_ptr())
@@ -334,6 +362,8 @@ def test_jump_full_size_sampled(gen):
     np.testing.assert_array_equal(got, ref)
     if gen == "ggl":
         assert int(got[np.searchsorted(pos, 9999)]) == 1043618065
+    if gen == "mt19937":
+        assert int(got[np.searchsorted(pos, 9999)]) == 4123659995
     del out
 
 
