@@ -284,6 +284,41 @@ def measure_xor128_jump(P, torch, out_u, h_xor, stream):
             "skip_2p40": {"streams": N_STREAMS, "ms": skip_ms}}
 
 
+def measure_ising_fused(P, torch, out_u, stream, L=4096):
+    """Checkerboard Metropolis sweeps of a 4096 x 4096 lattice: the draws
+    stored (prng_fill_u32 then prng_ising_half_sweep, the serving path) or
+    consumed where they are made (prng_ising_fused), per generator and
+    stream count.  ms per sweep (two half-sweeps, 2^24 site updates)."""
+    sid = stream.cuda_stream
+    t4, t8 = P.prng_ising_thresholds(0.4406868)
+    spins = torch.ones((L, L), dtype=torch.int8, device=out_u.device)
+    draws = out_u[: L * L // 2]
+    res = {"L": L, "runs": []}
+    for g, lux, ns in [("ggl", 0, 1024), ("ggl", 0, 65536), ("xor128", 0, 65536),
+                       ("ranecu", 0, 65536), ("ranmar", 0, 65536), ("ranlux", 223, 65536),
+                       ("mt19937", 0, 8192)]:
+        h = P.prng_create(g, SEED, ns, lux)
+        per = L * L // (2 * ns)
+
+        def stored():
+            for colour in (0, 1):
+                P.prng_fill_u32(h, draws.data_ptr(), per, sid)
+                P.prng_ising_half_sweep([{"d_spins": spins, "d_draws": draws, "L": L,
+                                          "colour": colour, "gen": g, "t4": t4, "t8": t8}], sid)
+
+        def fused():
+            for colour in (0, 1):
+                P.prng_ising_fused(h, spins, L, colour, t4, t8, sid)
+
+        ms_s = _time_ms(torch, stream, stored, reps=5, warm=2)
+        ms_f = _time_ms(torch, stream, fused, reps=5, warm=2)
+        P.prng_destroy(h)
+        res["runs"].append({"gen": g, "luxury": lux, "streams": ns, "ms_per_sweep_stored": ms_s,
+                            "ms_per_sweep_fused": ms_f,
+                            "site_updates_per_s_fused": L * L / (ms_f / 1e3)})
+    return res
+
+
 def measure_mt_jump(P, torch, out_u, h_mt, stream):
     """MT19937 jump-ahead over GF(2): prng_skip(2^40) of the 8,192-stream
     handle (the jump polynomial applied to every table), and the
@@ -465,6 +500,7 @@ def run_ours(args, rank, world, local_rank):
     xor128_jump = measure_xor128_jump(P, torch, out_u, handles["xor128"], stream)
     f64 = measure_f64(P, torch, out_u, handles, seed_r, stream)
     mt_jump = measure_mt_jump(P, torch, out_u, handles["mt19937"], stream)
+    ising_fused = measure_ising_fused(P, torch, out_u, stream)
 
     # Batched requests (20,000 mixed fills): one graph launch vs one plain
     # re-seed + fill per request.
@@ -523,6 +559,7 @@ def run_ours(args, rank, world, local_rank):
         "xor128_jump": xor128_jump,
         "f64": f64,
         "mt_jump": mt_jump,
+        "ising_fused": ising_fused,
         "tiles": {"tuned_cache": bool(tuned),
                   **{g: list(P.prng_get_tile(g, RANLUX_P if g == "ranlux" else 0)) for g in GENS}},
     }

@@ -233,6 +233,18 @@ typedef struct prng_ising_req {
  * The descriptors are passed by value to the kernels (no allocation). */
 int prng_ising_half_sweep(const prng_ising_req *reqs, uint32_t n, void *stream);
 
+/* Fused half-sweep (the paper's "virtualised" generator, Section 3.1: draws
+ * consumed where they are made, never stored): one half-sweep of colour
+ * `colour` of the L x L lattice d_spins, site of colour rank k taking draw
+ * k of the handle's next stream-major block of L*L/2 draws (n_per_stream =
+ * L*L/(2 n_streams) per stream), which also advances the handle.  The
+ * lattice ends bit-identical to prng_fill_u32 of that block followed by
+ * prng_ising_half_sweep with the generator's shift (7 for GGL and RANECU, 8
+ * for XOR128 and MT19937, 0 for RANMAR and RANLUX).  L even, 2 <= L <=
+ * 65534, L*L/2 a multiple of n_streams (PRNG_ESIZE otherwise). */
+int prng_ising_fused(prng_state *st, int8_t *d_spins, uint32_t L, uint32_t colour, uint32_t t4,
+                     uint32_t t8, void *stream);
+
 /* t4 = floor(2^24 exp(-4 beta)), t8 = floor(2^24 exp(-8 beta)), in double. */
 int prng_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8);
 

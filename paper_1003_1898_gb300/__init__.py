@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         "prng_batcher_launch": ([vp, ctypes.POINTER(PrngFillReq), u32, vp], ctypes.c_int),
         "prng_batcher_destroy": ([vp], None),
         "prng_ising_half_sweep": ([ctypes.POINTER(PrngIsingReq), u32, vp], ctypes.c_int),
+        "prng_ising_fused": ([vp, vp, u32, u32, u32, u32, vp], ctypes.c_int),
         "prng_ising_thresholds": ([ctypes.c_double, ctypes.POINTER(u32), ctypes.POINTER(u32)],
                                   ctypes.c_int),
         "prng_destroy": ([vp], None),
@@ -279,6 +280,13 @@ def prng_ising_half_sweep(reqs, stream=None):
         arr[i].t4 = r["t4"]
         arr[i].t8 = r["t8"]
     _check(lib().prng_ising_half_sweep(arr, len(reqs), _stream(stream)), "prng_ising_half_sweep")
+
+
+def prng_ising_fused(h, spins, L: int, colour: int, t4: int, t8: int, stream=None):
+    """One half-sweep of the lattice consuming the handle's next L*L/2 draws
+    where they are made (no draw buffer)."""
+    _check(lib().prng_ising_fused(h, _ptr(spins), L, colour, t4, t8, _stream(stream)),
+           "prng_ising_fused")
 
 
 def prng_destroy(h):

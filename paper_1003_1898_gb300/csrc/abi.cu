@@ -213,6 +213,52 @@ int prng_fill_f64(prng_state* st, double* d_out, uint64_t n_per_stream, void* st
   return fill_impl(st, d_out, n_per_stream, OUT_F64, static_cast<cudaStream_t>(stream));
 }
 
+int prng_ising_fused(prng_state* st, int8_t* d_spins, uint32_t L, uint32_t colour, uint32_t t4,
+                     uint32_t t8, void* stream) {
+  if (st == nullptr || d_spins == nullptr) return PRNG_ENULL;
+  if (L < 2 || (L & 1) != 0 || L > 65534 || colour > 1) return PRNG_ESIZE;
+  const uint64_t sites = (uint64_t)L * (L / 2);
+  if (sites % st->n_streams != 0) return PRNG_ESIZE;
+  static const uint32_t kShift[6] = {7, 8, 7, 0, 0, 8};   // 24-bit value of a draw
+  FillDesc d{};
+  d.state = st->d_state;
+  d.n_rows = st->n_streams;
+  d.n_per = sites / st->n_streams;
+  d.out = d_spins;          // never written as words: the sink takes every draw
+  d.pitch = d.n_per;
+  d.limit = sites;
+  d.pos = st->pos;
+  d.p = st->p;
+  d.mode = OUT_ISING;
+  d.jump = 0;
+  IsingSink& q = d.ising;
+  q.spins = d_spins;
+  q.L = L;
+  q.half = L / 2;
+  q.lg_half = 32;
+  if ((q.half & (q.half - 1)) == 0)
+    for (uint32_t b = 0; b < 32; b++)
+      if ((1u << b) == q.half) q.lg_half = b;
+  q.colour = colour;
+  q.shift = kShift[st->gen];
+  q.t4 = t4;
+  q.t8 = t8;
+  const Tile t = default_tile(st->gen, st->p);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (st->gen) {
+    case RANMAR: e = launch_fill_ranmar(d, t, s); break;
+    case RANLUX: e = launch_fill_ranlux(d, t, s); break;
+    case MT19937: e = launch_fill_mt(d, t, s); break;
+    default:
+      e = t.cols == 128 ? launch_fill_mlcg(st->gen, d, t, s) : launch_fill_simple(st->gen, d, t, s);
+      break;
+  }
+  if (e != cudaSuccess) return PRNG_ECUDA;
+  st->pos = advance_pos(st->gen, st->pos, d.n_per);
+  return PRNG_OK;
+}
+
 // XOR128 skips of at least this many steps use the GF(2) matrix power
 // (about 128 column XORs per stream) instead of stepping.
 constexpr uint64_t kXor128MatrixSkip = 256;

@@ -34,7 +34,8 @@ constexpr int kWords[6] = {1, 4, 2, 98, 25, 624};
 // double (reading R11): the kernels run the u32 pipeline over 2 n draws
 // per stream and convert each aligned pair (u32 slots 2k, 2k+1) into the
 // double that occupies the same 8 bytes.
-enum OutMode : int { OUT_U32 = 0, OUT_F32 = 1, OUT_F64 = 2 };
+// OUT_ISING consumes each draw in place (see IsingSink) instead of storing it.
+enum OutMode : int { OUT_U32 = 0, OUT_F32 = 1, OUT_F64 = 2, OUT_ISING = 3 };
 
 // Calls fn(std::integral_constant<int, mode>) for a run-time mode.
 template <class Fn>
@@ -42,9 +43,22 @@ inline auto with_mode(int mode, Fn&& fn) {
   switch (mode) {
     case OUT_F64: return fn(std::integral_constant<int, OUT_F64>{});
     case OUT_F32: return fn(std::integral_constant<int, OUT_F32>{});
+    case OUT_ISING: return fn(std::integral_constant<int, OUT_ISING>{});
     default: return fn(std::integral_constant<int, OUT_U32>{});
   }
 }
+
+// The consumer of a fused Metropolis half-sweep (OUT_ISING): the draw for
+// the site of colour rank k of an L x L checkerboard lattice updates that
+// site at once instead of being stored.
+struct IsingSink {
+  int8_t* spins;       // L x L, row-major, +1/-1
+  uint32_t L, half;    // side, L / 2
+  uint32_t lg_half;    // log2(half) when half is a power of two, else 32
+  uint32_t colour;     // sites with (x + y) % 2 == colour
+  uint32_t shift;      // 24-bit acceptance value = draw >> shift
+  uint32_t t4, t8;     // integer thresholds for dE = 4 and dE = 8
+};
 
 // One fill (or skip, or jump fill) as the kernels see it.
 struct FillDesc {
@@ -59,6 +73,7 @@ struct FillDesc {
   int32_t p;           // RANLUX luxury p
   int32_t mode;        // OutMode: u32 words, floats, or doubles from pairs
   int32_t jump;        // 1: rows are chunks of one jump-ahead sequence
+  IsingSink ising;     // OUT_ISING: where element k (= colour rank k) goes
 };
 
 // Launch configuration of a fill kernel (chosen by the tuner or defaults).
@@ -211,6 +226,44 @@ __device__ __forceinline__ void st_chunk(uint32_t* p, uint4 v) {
   else st_out4(p, v);
 }
 
+// Metropolis update of the site of colour rank k with draw v (the same rule
+// as k_ising_half_sweep): accept when dE = 2 s (sum of neighbours) <= 0, or
+// the 24-bit value v >> shift is below t4 (dE = 4) or t8 (dE = 8).  Sites of
+// one colour only neighbour the other colour, so updates of one half-sweep
+// never race.
+__device__ __forceinline__ void ising_site(const IsingSink& q, uint32_t k, uint32_t v) {
+  const uint32_t L = q.L, half = q.half;
+  const uint32_t y = q.lg_half < 32 ? k >> q.lg_half : k / half;
+  const uint32_t x = 2 * (k - y * half) + ((y + q.colour) & 1u);
+  const uint32_t yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+  const uint32_t xl = x == 0 ? L - 1 : x - 1, xr = x + 1 == L ? 0 : x + 1;
+  int8_t* row = q.spins + (uint64_t)y * L;
+  const int s = row[x];
+  const int nb = q.spins[(uint64_t)yu * L + x] + q.spins[(uint64_t)yd * L + x] + row[xl] + row[xr];
+  const int dE = 2 * s * nb;
+  const uint32_t r = v >> q.shift;
+  if (dE <= 0 || (dE == 4 ? r < q.t4 : r < q.t8)) row[x] = (int8_t)(-s);
+}
+
+// Output of four consecutive draws (element index e of the first, at p) or
+// of one: stored, or consumed by the fused half-sweep.
+template <int OM, int WB>
+__device__ __forceinline__ void put4(const FillDesc& d, uint32_t* p, uint64_t e, uint4 v) {
+  if constexpr (OM == OUT_ISING) {
+    ising_site(d.ising, (uint32_t)e, v.x);
+    ising_site(d.ising, (uint32_t)e + 1, v.y);
+    ising_site(d.ising, (uint32_t)e + 2, v.z);
+    ising_site(d.ising, (uint32_t)e + 3, v.w);
+  } else {
+    st_chunk<OM, WB>(p, v);
+  }
+}
+template <int OM>
+__device__ __forceinline__ void put1(const FillDesc& d, uint32_t* p, uint64_t e, uint32_t v) {
+  if constexpr (OM == OUT_ISING) ising_site(d.ising, (uint32_t)e, v);
+  else st_out(p, v);
+}
+
 // Row-major staging tile: thread t's staged draws in row t (SPW words per
 // row, SPW = 4 mod 8 so that eight threads storing the same 16-byte chunk
 // of their rows hit eight different bank quads).  RowFlusher writes tile
@@ -226,6 +279,10 @@ __device__ __forceinline__ void st_chunk(uint32_t* p, uint4 v) {
 // even, so a pair is never split by a flush or a cut.
 template <int T, int SPW, bool LIMITED = false, int OM = OUT_U32, int WB = 32>
 struct RowFlusher {
+  const FillDesc* dp;  // OUT_ISING: the sink
+  uint64_t ebase;      // element index of this lane's first row, column 0
+  const uint32_t* tile;              // OUT_ISING: the whole tile, rows row0 ..
+  uint64_t irow0, ipitch, irows;     //   and their rows in the output
   static_assert(SPW % 8 == 4, "row pitch must be 4 mod 8 words");
   static constexpr int NW = T / 32, RIT = T / (4 * NW);
   uint32_t* gp;        // this lane's first row, column 0
@@ -236,13 +293,20 @@ struct RowFlusher {
   bool vec_ok;
 
   __device__ __forceinline__ void init(const uint32_t* s, uint32_t* out, uint64_t pitch,
-                                       uint64_t row0, uint64_t n_rows, uint64_t limit) {
+                                       uint64_t row0, uint64_t n_rows, uint64_t limit,
+                                       const FillDesc* d = nullptr) {
     // A quarter-warp (one 16-byte shared access phase) reads eight chunks of
     // one row: bank quads r * SPW / 4 + chunk (mod 8), all different.
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int r = wi * 4 + (lane >> 3);
     qq = lane & 7;
     rowstep = (uint64_t)NW * 4 * pitch;
+    dp = d;
+    ebase = (row0 + r) * pitch;
+    tile = s;
+    irow0 = row0;
+    ipitch = pitch;
+    irows = n_rows;
     gp = out + (row0 + r) * pitch;
     sp = s + r * SPW;
     uint64_t rows = n_rows;
@@ -290,7 +354,10 @@ struct RowFlusher {
             for (int i = 0; i < 4; i++) v[i] = u[A + i];
           }
           if (!LIMITED || k != kcut || gc + 4 <= ccut) {
-            st_chunk<OM, WB>(g + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
+            if constexpr (OM == OUT_ISING)
+              put4<OM, WB>(*dp, nullptr, ebase + gc + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
+            else
+              st_chunk<OM, WB>(g + k * rowstep, make_uint4(v[0], v[1], v[2], v[3]));
             continue;
           }
         }
@@ -305,8 +372,12 @@ struct RowFlusher {
 #pragma unroll
           for (int i = 0; i < 4; i++) {
             const int ci = c + i;
-            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut))
-              st_out(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci]);
+            if (ci >= 0 && ci < w && (!LIMITED || k != kcut || gc + i < ccut)) {
+              if constexpr (OM == OUT_ISING)
+                ising_site(dp->ising, (uint32_t)(ebase + gc + k * rowstep + i), sp[k * NW * 4 * SPW + ci]);
+              else
+                st_out(g + k * rowstep + i, sp[k * NW * 4 * SPW + ci]);
+            }
           }
         }
       }
@@ -314,11 +385,30 @@ struct RowFlusher {
   }
 
   __device__ __forceinline__ void flush(uint64_t g0, int w) const {
-    switch ((uint32_t)(0u - (uint32_t)g0) & 3u) {
-      case 0: flush_a<0>(g0, w); break;
-      case 2: flush_a<2>(g0, w); break;
-      case 1: if constexpr (OM != OUT_F64) flush_a<1>(g0, w); break;
-      default: if constexpr (OM != OUT_F64) flush_a<3>(g0, w); break;
+    if constexpr (OM == OUT_ISING) {
+      // The fused half-sweep: every staged draw updates its site.  The
+      // CTA's threads take the tile's elements in row order (consecutive
+      // threads, consecutive colour ranks), stepping (row, column) by T
+      // elements without a division per element.
+      const int qT = T / w, rT = T - qT * w;
+      int r = threadIdx.x / w, c = threadIdx.x - r * w;
+      for (int i = threadIdx.x; i < T * w; i += T) {
+        if (irow0 + r < irows)
+          ising_site(dp->ising, (uint32_t)((irow0 + r) * ipitch + g0) + (uint32_t)c, tile[r * SPW + c]);
+        r += qT;
+        c += rT;
+        if (c >= w) {
+          c -= w;
+          r++;
+        }
+      }
+    } else {
+      switch ((uint32_t)(0u - (uint32_t)g0) & 3u) {
+        case 0: flush_a<0>(g0, w); break;
+        case 2: flush_a<2>(g0, w); break;
+        case 1: if constexpr (OM != OUT_F64) flush_a<1>(g0, w); break;
+        default: if constexpr (OM != OUT_F64) flush_a<3>(g0, w); break;
+      }
     }
   }
 };

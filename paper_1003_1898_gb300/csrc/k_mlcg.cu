@@ -74,12 +74,14 @@ struct LjConst {
 // warp: draws 0 .. nv-1 written to orow (row start), 16-byte stores when vec.
 template <class G, int OM>
 __device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&base)[G::NC], int lane,
-                                       uint32_t* orow, uint64_t nv, bool vec) {
+                                       uint32_t* orow, uint64_t nv, bool vec, const FillDesc& d,
+                                       uint64_t erow) {
   constexpr int NC = G::NC;
   uint32_t s[NC];
 #pragma unroll
   for (int c = 0; c < NC; c++) s[c] = G::mul(c, K.lane_mul[c], base[c]);
   orow += 4 * lane;
+  erow += 4 * lane;
   for (uint64_t c0 = 0; c0 < nv; c0 += 128) {
     uint32_t t[NC], o[4];
 #pragma unroll
@@ -91,7 +93,15 @@ __device__ __forceinline__ void lj_row(const LjConst<G>& K, const uint32_t (&bas
       for (int c = 0; c < NC; c++) t[c] = G::step(c, t[c]);
       o[i] = lj_conv<G, OM>(G::out(t));
     }
-    if (vec && c0 + 128 <= nv) {
+    if constexpr (OM == OUT_ISING) {
+      if (c0 + 128 <= nv) {
+        put4<OM, 31>(d, nullptr, erow + c0, make_uint4(o[0], o[1], o[2], o[3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (c0 + 4 * lane + i < nv) put1<OM>(d, nullptr, erow + c0 + i, o[i]);
+      }
+    } else if (vec && c0 + 128 <= nv) {
       st_chunk<OM, 31>(orow + c0, make_uint4(o[0], o[1], o[2], o[3]));
     } else if constexpr (OM == OUT_F64) {   // nv is even: pairs are whole
 #pragma unroll
@@ -119,7 +129,7 @@ __device__ __forceinline__ void lj_stream(const LjConst<G>& K, const FillDesc& d
   if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool vec = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  lj_row<G, OM>(K, base, lane, out + row * d.pitch, nv, vec);
+  lj_row<G, OM>(K, base, lane, out + row * d.pitch, nv, vec, d, row * d.pitch);
   if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < NC; c++) d.state[c * d.n_rows + row] = G::mul(c, base[c], K.fin_mul[c]);
@@ -150,7 +160,8 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
   for (uint64_t row = wrow; row < d.n_rows; row += nwarps) {
     uint64_t nv = d.n_per;
     if (d.limit - row * d.pitch < nv) nv = d.limit - row * d.pitch;
-    lj_row<G, OM>(K, jrow, lane, out + row * d.pitch, nv, vec_ok && ((row * d.pitch) & 3) == 0);
+    lj_row<G, OM>(K, jrow, lane, out + row * d.pitch, nv, vec_ok && ((row * d.pitch) & 3) == 0, d,
+                  row * d.pitch);
 #pragma unroll
     for (int c = 0; c < NC; c++) jrow[c] = G::mul(c, jrow[c], jstep[c]);
   }

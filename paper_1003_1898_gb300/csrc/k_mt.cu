@@ -45,7 +45,8 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
 // tempered and, if o != null, written to o[k] (16-byte stores when VEC);
 // PARTIAL: only entries k < take are written.
 template <int OM, bool PARTIAL>
-__device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec) {
+__device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec,
+                                         const FillDesc* d = nullptr, uint64_t e0 = 0) {
 #pragma unroll
   for (int k0 = 0; k0 < 640; k0 += 128) {
     const int k = k0 + 4 * lane;
@@ -80,7 +81,16 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
         t.y = mt_conv<OM>(mt_temper(v.y));
         t.z = mt_conv<OM>(mt_temper(v.z));
         t.w = mt_conv<OM>(mt_temper(v.w));
-        if (!PARTIAL && vec) {
+        if constexpr (OM == OUT_ISING) {   // e0 + k: element index of word k
+          if (!PARTIAL) {
+            put4<OM, 32>(*d, nullptr, e0 + k, t);
+          } else {
+            if (k < take) put1<OM>(*d, nullptr, e0 + k, t.x);
+            if (k + 1 < take) put1<OM>(*d, nullptr, e0 + k + 1, t.y);
+            if (k + 2 < take) put1<OM>(*d, nullptr, e0 + k + 2, t.z);
+            if (k + 3 < take) put1<OM>(*d, nullptr, e0 + k + 3, t.w);
+          }
+        } else if (!PARTIAL && vec) {
           st_chunk<OM, 32>(o + k, t);
         } else {
           if constexpr (OM == OUT_F64) {   // take and the table offset are even
@@ -123,20 +133,23 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
         if constexpr (OM == OUT_F64) {
           if ((k & 1) == 0) st_pair<32>(orow + k, mt_temper(s[mti + k]), mt_temper(s[mti + k + 1]));
         } else {
-          st_out(orow + k, mt_conv<OM>(mt_temper(s[mti + k])));
+          put1<OM>(d, orow + k, row * d.pitch + k, mt_conv<OM>(mt_temper(s[mti + k])));
         }
     j = h;
   }
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   const bool vec = store && ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   while (n - j >= 624) {
-    if (j + 624 <= nv) mt_twist<OM, false>(s, lane, store ? orow + j : nullptr, 624, vec);
-    else mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false);
+    if (j + 624 <= nv)
+      mt_twist<OM, false>(s, lane, store ? orow + j : nullptr, 624, vec, &d, row * d.pitch + j);
+    else
+      mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false, &d,
+                         row * d.pitch + j);
     j += 624;
   }
   if (j < n) {
     const uint64_t take = nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
-    mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)take, false);
+    mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)take, false, &d, row * d.pitch + j);
   }
   for (int k = lane; k < 624; k += 32) gs[k] = s[k];
   __syncwarp();

@@ -93,7 +93,7 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
         const uint32_t vb = __shfl_down_sync(0xFFFFFFFFu, v, 1);
         if (on && !(l & 1) && (!LIMITED || rbase + col < d.limit)) st_pair<24>(orow + col, v, vb);
       } else {
-        if (on && (!LIMITED || rbase + col < d.limit)) st_out(orow + col, v);
+        if (on && (!LIMITED || rbase + col < d.limit)) put1<OM>(d, orow + col, rbase + col, v);
       }
     };
     uint64_t g = 0;

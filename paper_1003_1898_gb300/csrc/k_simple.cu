@@ -142,13 +142,18 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
       for (int c = 0; c < w; c++) my[4 * ((c >> 2) ^ sw) + (c & 3)] = conv<G, OM>(g.next());
     }
     __syncthreads();
-    if (w == K && vec_ok && last_row * d.pitch + c0 + K <= d.limit) {
+    if (w == K && (vec_ok || OM == OUT_ISING) && last_row * d.pitch + c0 + K <= d.limit) {
       const uint32_t* src = t + cr0 * K + 4 * cslot;
       uint32_t* dst = cg + c0;
+      const uint64_t edst = (row0 + cr0) * d.pitch + 4 * cch + c0;
 #pragma unroll
       for (int k = 0; k < CH; k++)
-        if (k < crows)
-          st_chunk<OM, G::WB>(dst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
+        if (k < crows) {
+          if constexpr (OM == OUT_ISING)
+            put4<OM, G::WB>(d, nullptr, edst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
+          else
+            st_chunk<OM, G::WB>(dst + k * cstep, *reinterpret_cast<const uint4*>(src + k * RS * K));
+        }
     } else {
       // Partial tile, unaligned output or a jump fill's last chunk: scalar
       // stores, warp per row, lanes on consecutive columns.
@@ -165,7 +170,8 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
                              t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3) + 1]);
         } else {
           for (int c = lane; c < w; c += 32)
-            if (base + c < d.limit) st_out(out + base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)]);
+            if (base + c < d.limit)
+              put1<OM>(d, out + base + c, base + c, t[r * K + 4 * ((c >> 2) ^ (r & 7)) + (c & 3)]);
         }
       }
     }

@@ -202,7 +202,7 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool store = out != nullptr;
   RowFlusher<T, SPW, LIMITED, OM, 24> fl;
-  fl.init(smem, out, d.pitch, row0, nr, d.limit);
+  fl.init(smem, out, d.pitch, row0, nr, d.limit, &d);
   uint32_t* my = smem + tid * SPW;            // this thread's tile row
   uint32_t* ring = my + 24;                   // scratch ring in columns 24..47
 

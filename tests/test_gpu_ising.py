@@ -80,3 +80,65 @@ def test_ising_rejects_bad_lattices():
     with pytest.raises(P.PrngError):
         P.prng_ising_half_sweep([{"d_spins": s, "d_draws": d, "L": 4, "colour": 2, "shift": 0,
                                   "t4": 0, "t8": 0}])
+
+
+# ------------------------------------------------------------ fused half-sweeps
+
+def gpu_fused_run(gen, seed, n_streams, L, sweeps, lux=0, beta=oracle.ISING_BETA):
+    t4, t8 = P.prng_ising_thresholds(beta)
+    h = P.prng_create(gen, seed, n_streams, lux)
+    spins = torch.ones((L, L), dtype=torch.int8, device="cuda")
+    em = []
+    try:
+        for sw in range(sweeps):
+            for colour in (0, 1):
+                P.prng_ising_fused(h, spins, L, colour, t4, t8)
+            s = spins.cpu().numpy()
+            em.append((oracle.ising_energy(s), oracle.ising_magnetisation(s)))
+    finally:
+        P.prng_destroy(h)
+    return spins.cpu().numpy(), em
+
+
+@pytest.mark.parametrize("gen,lux", [("ggl", 0), ("xor128", 0), ("ranecu", 0), ("ranmar", 0),
+                                     ("ranlux", 223), ("ranlux", 24), ("mt19937", 0)])
+@pytest.mark.parametrize("L,ns", [(64, 32), (96, 48), (256, 1024), (130, 65)])
+def test_fused_run_equals_oracle(gen, lux, L, ns):
+    # Draws consumed where they are made give the same lattice after every
+    # sweep as the stored draws and the oracle.
+    got, em = gpu_fused_run(gen, 321, ns, L, 5, lux)
+    want, em_want = oracle.ising_run(gen, 321, ns, L, 5, luxury=lux)
+    np.testing.assert_array_equal(got, want)
+    assert em == em_want
+
+
+@pytest.mark.parametrize("gen", ["ggl", "xor128", "ranmar", "mt19937"])
+def test_fused_then_fill_continues_the_stream(gen):
+    # A fused half-sweep advances the handle like the fill it replaces.
+    L, ns = 64, 32
+    t4, t8 = P.prng_ising_thresholds(0.44)
+    a = P.prng_create(gen, 9, ns, 0)
+    b = P.prng_create(gen, 9, ns, 0)
+    try:
+        P.prng_ising_fused(a, torch.ones((L, L), dtype=torch.int8, device="cuda"), L, 0, t4, t8)
+        P.prng_skip(b, L * L // (2 * ns))
+        x = torch.empty(ns * 50, dtype=torch.int32, device="cuda")
+        y = torch.empty(ns * 50, dtype=torch.int32, device="cuda")
+        P.prng_fill_u32(a, x, 50)
+        P.prng_fill_u32(b, y, 50)
+        torch.cuda.synchronize()
+        assert torch.equal(x, y)
+    finally:
+        P.prng_destroy(a)
+        P.prng_destroy(b)
+
+
+def test_fused_rejects_bad_shapes():
+    h = P.prng_create("ggl", 1, 48, 0)
+    s = torch.ones((64, 64), dtype=torch.int8, device="cuda")
+    try:
+        for L, colour in [(63, 0), (64, 2), (0, 0), (10, 0)]:     # odd, colour, empty, 50 % 48
+            with pytest.raises(P.PrngError):
+                P.prng_ising_fused(h, s, L, colour, 1, 1)
+    finally:
+        P.prng_destroy(h)
