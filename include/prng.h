@@ -227,6 +227,13 @@ typedef struct prng_ising_req {
   uint32_t shift;
   uint32_t t4;
   uint32_t t8;
+  /* Layout of the draws: pitch = 0 means site k takes d_draws[k] (one
+   * stream-major block).  Otherwise site k takes d_draws[(k / per) * pitch
+   * + k % per]: the half-sweep's block of per draws per stream sits inside
+   * rows of `pitch` words, so one fill of several half-sweeps' draws serves
+   * them all (d_draws pointing at the half-sweep's column offset). */
+  uint32_t per;
+  uint32_t pitch;
 } prng_ising_req;
 
 /* One half-sweep of each of the n lattices, asynchronously on `stream`.

@@ -28,7 +28,7 @@ class PrngIsingReq(ctypes.Structure):
     """struct prng_ising_req (include/prng.h)."""
     _fields_ = [("d_spins", ctypes.c_void_p), ("d_draws", ctypes.c_void_p), ("L", ctypes.c_uint32),
                 ("colour", ctypes.c_uint32), ("shift", ctypes.c_uint32), ("t4", ctypes.c_uint32),
-                ("t8", ctypes.c_uint32)]
+                ("t8", ctypes.c_uint32), ("per", ctypes.c_uint32), ("pitch", ctypes.c_uint32)]
 
 
 class PrngFillReq(ctypes.Structure):
@@ -268,7 +268,9 @@ def prng_ising_thresholds(beta: float):
 
 def prng_ising_half_sweep(reqs, stream=None):
     """reqs: iterable of dicts with d_spins, d_draws, L, colour, gen (or
-    shift), t4, t8."""
+    shift), t4, t8, and optionally per and pitch (the draws of the
+    half-sweep as per-word columns of rows `pitch` words apart); d_draws may
+    be an integer device address."""
     reqs = list(reqs)
     arr = (PrngIsingReq * max(1, len(reqs)))()
     for i, r in enumerate(reqs):
@@ -279,6 +281,8 @@ def prng_ising_half_sweep(reqs, stream=None):
         arr[i].shift = r["shift"] if "shift" in r else SHIFT[_gen(r["gen"])]
         arr[i].t4 = r["t4"]
         arr[i].t8 = r["t8"]
+        arr[i].per = r.get("per", 0)
+        arr[i].pitch = r.get("pitch", 0)
     _check(lib().prng_ising_half_sweep(arr, len(reqs), _stream(stream)), "prng_ising_half_sweep")
 
 

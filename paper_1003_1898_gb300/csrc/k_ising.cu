@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kIsingThreads) k_ising_half_sweep(const __grid
     const int s = row[x];
     const int nb = q.d_spins[(uint64_t)yu * L + x] + q.d_spins[(uint64_t)yd * L + x] + row[xl] + row[xr];
     const int dE = 2 * s * nb;
-    const uint32_t r = q.d_draws[k] >> q.shift;
+    const uint64_t di = q.pitch == 0 ? k : (k / q.per) * q.pitch + k % q.per;
+    const uint32_t r = q.d_draws[di] >> q.shift;
     const bool accept = dE <= 0 || (dE == 4 ? r < q.t4 : r < q.t8);
     if (accept) row[x] = (int8_t)(-s);
   }
@@ -71,6 +72,7 @@ extern "C" int prng_ising_half_sweep(const prng_ising_req* reqs, uint32_t n, voi
     const prng_ising_req& q = reqs[i];
     if (q.d_spins == nullptr || q.d_draws == nullptr) return PRNG_ENULL;
     if (q.L < 2 || (q.L & 1) != 0 || q.colour > 1 || q.shift > 8) return PRNG_ESIZE;
+    if (q.pitch != 0 && (q.per == 0 || q.per > q.pitch)) return PRNG_ESIZE;
     if ((reinterpret_cast<uintptr_t>(q.d_draws) & 3) != 0) return PRNG_ESIZE;
   }
   const cudaStream_t s = static_cast<cudaStream_t>(stream);

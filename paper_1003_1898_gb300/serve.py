@@ -9,10 +9,12 @@ consuming the client's next L*L/2 draws (L*L/(2 n_streams) per stream).
 
 The loop works in ticks.  A tick admits arrived requests in arrival order
 while their client is free and the state-plus-output memory stays under the
-cap, advances every running Ising request by one half-sweep, and enqueues
-one batched fill (prng_batcher_launch: the new fills plus the draws of all
-running Ising half-sweeps) and one batched half-sweep
-(prng_ising_half_sweep) on the server's stream.  Up to `max_inflight` ticks
+cap, advances every running Ising request by up to `half_sweeps_per_tick`
+half-sweeps, and enqueues one batched fill (prng_batcher_launch: the new
+fills plus, per running Ising request, one fill holding the draws of all its
+half-sweeps of the tick, each half-sweep's block a column range of the
+stream rows) and then one batched half-sweep launch (prng_ising_half_sweep)
+per half-sweep step on the server's stream.  Up to `max_inflight` ticks
 are on the GPU while the host forms the next, so requests that arrive while
 others run join the next tick.  A client's requests are served in order and
 only its own requests touch its streams, so every result is the same as the
@@ -69,10 +71,14 @@ class Client:
 class Server:
     def __init__(self, client_specs, n_streams: int = 1024, mem_cap: float = 40e9,
                  max_inflight: int = 2, beta: float = ISING_BETA, keep_results: bool = False,
-                 max_active: int = 0):
+                 max_active: int = 0, half_sweeps_per_tick: int = 1):
         """max_active > 0 caps the requests in progress (1 = a plain FIFO queue,
         one request at a time, the baseline continuous batching is measured
-        against)."""
+        against).  half_sweeps_per_tick: Ising half-sweeps a running request
+        advances per tick.  More means fewer ticks per run, but longer ticks
+        that later arrivals wait behind; with the GPU busy on half-sweeps
+        (the benchmark's mix), 1 gives the lowest latency at the same
+        throughput."""
         import torch
         self.torch = torch
         self.clients = [Client(i, g, lux, seed, n_streams)
@@ -83,6 +89,7 @@ class Server:
         self.mem_used = self.mem_state
         self.max_inflight = max_inflight
         self.max_active = max_active
+        self.hpt = max(1, int(half_sweeps_per_tick))
         self.keep = keep_results
         self.t4, self.t8 = prng_ising_thresholds(beta)
         self.stream = torch.cuda.Stream()
@@ -104,10 +111,11 @@ class Server:
         per = -(-n // self.n_streams)
         return per, self.n_streams * per
 
-    def _bytes(self, r: Request) -> int:
+    def request_bytes(self, r: Request) -> int:
+        """Device bytes a request holds while it runs (counted against the cap)."""
         if r.kind == "fill":
             return 4 * self._fill_shape(r.n)[1]
-        return r.L * r.L + 2 * r.L * r.L          # int8 lattice + L*L/2 u32 draws
+        return r.L * r.L + self.hpt * 2 * r.L * r.L   # int8 lattice + draws of hpt half-sweeps
 
     # ------------------------------------------------------------------ run
     def run(self, requests, realtime: bool = True):
@@ -142,7 +150,7 @@ class Server:
                 for r in finishing:
                     r.done = t
                     left -= 1
-                    self.mem_used -= self._bytes(r)
+                    self.mem_used -= self.request_bytes(r)
                     if not self.keep:
                         r.out = r.spins = None
                     r.draws = None
@@ -157,26 +165,38 @@ class Server:
             if len(inflight) >= self.max_inflight:
                 retire(True)
                 continue
-            fills, sweeps, finishing = [], [], []
+            fills, steps, finishing = [], [], []
             taken = set()
-            for r in running:                  # next half-sweep of each running Ising run
-                c = self.clients[r.client]
-                taken.add(r.client)
-                fills.append({"st": c.handle, "d_out": r.draws,
-                              "n_per_stream": r.L * r.L // (2 * self.n_streams)})
-                sweeps.append({"d_spins": r.spins, "d_draws": r.draws, "L": r.L,
-                               "colour": r.half_done % 2, "shift": SHIFT[c.gen],
-                               "t4": self.t4, "t8": self.t8})
-                r.half_done += 1
-                r.numbers += r.L * r.L // 2
+
+            def ising_tick(r, c):
+                # The request's next h half-sweeps: one fill of h blocks per
+                # stream (row pitch h * per), then half-sweep t reads column
+                # block t of every row.
+                per = r.L * r.L // (2 * self.n_streams)
+                h = min(self.hpt, 2 * r.sweeps - r.half_done)
+                fills.append({"st": c.handle, "d_out": r.draws, "n_per_stream": h * per})
+                base = r.draws.data_ptr()
+                for t in range(h):
+                    while len(steps) <= t:
+                        steps.append([])
+                    steps[t].append({"d_spins": r.spins, "d_draws": base + 4 * t * per, "L": r.L,
+                                     "colour": (r.half_done + t) % 2, "shift": SHIFT[c.gen],
+                                     "t4": self.t4, "t8": self.t8, "per": per, "pitch": h * per})
+                r.half_done += h
+                r.numbers += h * (r.L * r.L // 2)
                 if r.half_done == 2 * r.sweeps:
                     finishing.append(r)
+
+            for r in running:                  # next half-sweeps of each running Ising run
+                c = self.clients[r.client]
+                taken.add(r.client)
+                ising_tick(r, c)
             keep = collections.deque()
             active = len(running) + sum(len(f) for _, f in inflight)
             while pending:                      # admission in arrival order
                 r = pending.popleft()
                 c = self.clients[r.client]
-                need = self._bytes(r)
+                need = self.request_bytes(r)
                 if self.max_active and active >= self.max_active:
                     keep.append(r)
                     continue
@@ -198,15 +218,12 @@ class Server:
                         finishing.append(r)
                     else:
                         r.spins = torch.ones((r.L, r.L), dtype=torch.int8, device="cuda")
-                        r.draws = torch.empty(r.L * r.L // 2, dtype=torch.int32, device="cuda")
+                        r.draws = torch.empty(self.hpt * (r.L * r.L // 2), dtype=torch.int32,
+                                              device="cuda")
                         c.busy = r
-                        fills.append({"st": c.handle, "d_out": r.draws,
-                                      "n_per_stream": r.L * r.L // (2 * self.n_streams)})
-                        sweeps.append({"d_spins": r.spins, "d_draws": r.draws, "L": r.L,
-                                       "colour": 0, "shift": SHIFT[c.gen],
-                                       "t4": self.t4, "t8": self.t8})
-                        r.half_done = 1
-                        r.numbers = r.L * r.L // 2
+                        r.half_done = 0
+                        r.numbers = 0
+                        ising_tick(r, c)
                         running.append(r)
             pending = keep
             if not fills:                       # nothing to launch now
@@ -222,8 +239,8 @@ class Server:
                 continue
             sid = self.stream.cuda_stream
             prng_batcher_launch(self.batcher, fills, sid)
-            if sweeps:
-                prng_ising_half_sweep(sweeps, sid)
+            for step in steps:                 # half-sweep t of every running lattice
+                prng_ising_half_sweep(step, sid)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(self.stream)
             inflight.append((ev, finishing))

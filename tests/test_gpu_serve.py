@@ -38,10 +38,13 @@ def _results(reqs):
     return out
 
 
-def test_mix_equals_oracle_and_clients_alone():
+@pytest.mark.parametrize("hpt", [1, 3])
+def test_mix_equals_oracle_and_clients_alone(hpt):
+    # hpt: Ising half-sweeps per tick (3: one fill of three half-sweeps' draws,
+    # read as column blocks of the stream rows, and three launches).
     specs = W.serving_clients(12, seed=99)
     reqs = _requests(80, 12, 1e9, seed=7)
-    srv = serve.Server(specs, n_streams=NS, keep_results=True)
+    srv = serve.Server(specs, n_streams=NS, keep_results=True, half_sweeps_per_tick=hpt)
     try:
         done = srv.run(reqs, realtime=False)
     finally:
@@ -67,7 +70,7 @@ def test_mix_equals_oracle_and_clients_alone():
     for c in sorted({r.client for r in done})[:4]:
         mine = [serve.Request(rid=r.rid, client=0, kind=r.kind, arrival=r.arrival, n=r.n,
                               f32=r.f32, L=r.L, sweeps=r.sweeps) for r in done if r.client == c]
-        alone_srv = serve.Server([specs[c]], n_streams=NS, keep_results=True)
+        alone_srv = serve.Server([specs[c]], n_streams=NS, keep_results=True)   # one per tick
         try:
             alone = _results(alone_srv.run(mine, realtime=False))
         finally:
@@ -103,7 +106,7 @@ def test_memory_cap_defers_admission():
     srv = serve.Server(specs, n_streams=NS, mem_cap=1, keep_results=True)
     try:
         state = srv.mem_state
-        srv.mem_cap = state + 3 * 128 * 128 + 1      # room for one lattice at a time
+        srv.mem_cap = state + srv.request_bytes(reqs[0]) + 1   # room for one lattice at a time
         done = srv.run(reqs, realtime=False)
     finally:
         srv.close()
