@@ -87,26 +87,37 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_sources_hash():
+# Sources that make up each generator's fill kernels (besides the shared
+# headers and the dispatch in abi.cu).
+KERNEL_SOURCES = {
+    "ggl": ["k_mlcg.cu", "k_simple.cu"], "ranecu": ["k_mlcg.cu", "k_simple.cu"],
+    "xor128": ["k_simple.cu"], "ranmar": ["k_ranmar.cu"],
+    "ranlux": ["ranlux.cuh", "k_ranlux.cu", f"k_ranlux_p{RANLUX_P}.cu"], "mt19937": ["k_mt.cu"],
+}
+SHARED_SOURCES = ["common.cuh", "batch.cuh", "abi.cu"]
+
+
+def kernel_sources_hash(gen):
+    """Hash of the sources a generator's fill kernels are built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1003_1898_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in SHARED_SOURCES + KERNEL_SOURCES[gen]:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(label):
+def recorded_traffic(label, gen):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of that generator's kernels; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
-        if t.get("sources") != kernel_sources_hash():
+        entry = t["per_launch"].get(label)
+        if entry is None or entry.get("sources") != kernel_sources_hash(gen):
             return None
-        return t["per_launch_bytes"].get(label)
+        return entry["bytes"]
     except Exception:
         return None
 
@@ -475,7 +486,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(items, key=lambda it: per[it[0]]["ms"])
     dl = dom[0]
     roof = {"kernel": dl, "bound": "hbm", "achieved": per[dl]["gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": per[dl]["frac_hbm"], "traffic": recorded_traffic(dl),
+            "unit": "GB/s", "frac": per[dl]["frac_hbm"], "traffic": recorded_traffic(dl, dom[1]),
             "peak_source": f"{peak_kind} hbm_gbs (copy, read+write)",
             "algorithmic_bytes_per_launch": algorithmic_bytes(*dom)}
 

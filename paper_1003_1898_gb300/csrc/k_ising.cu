@@ -54,7 +54,12 @@ __global__ void __launch_bounds__(kIsingThreads) k_ising_half_sweep(const __grid
     const int s = row[x];
     const int nb = q.d_spins[(uint64_t)yu * L + x] + q.d_spins[(uint64_t)yd * L + x] + row[xl] + row[xr];
     const int dE = 2 * s * nb;
-    const uint64_t di = q.pitch == 0 ? k : (k / q.per) * q.pitch + k % q.per;
+    uint64_t di = k;
+    if (q.pitch != 0) {   // k < 2^31: 32-bit quotient, a shift when per is a power of two
+      const uint32_t k32 = (uint32_t)k, per = q.per;
+      const uint32_t row = (per & (per - 1)) == 0 ? k32 >> (__ffs(per) - 1) : k32 / per;
+      di = (uint64_t)row * q.pitch + (k32 - row * per);
+    }
     const uint32_t r = q.d_draws[di] >> q.shift;
     const bool accept = dE <= 0 || (dE == 4 ? r < q.t4 : r < q.t8);
     if (accept) row[x] = (int8_t)(-s);

@@ -181,7 +181,8 @@ class Server:
                         steps.append([])
                     steps[t].append({"d_spins": r.spins, "d_draws": base + 4 * t * per, "L": r.L,
                                      "colour": (r.half_done + t) % 2, "shift": SHIFT[c.gen],
-                                     "t4": self.t4, "t8": self.t8, "per": per, "pitch": h * per})
+                                     "t4": self.t4, "t8": self.t8, "per": per,
+                                     "pitch": h * per if h > 1 else 0})
                 r.half_done += h
                 r.numbers += h * (r.L * r.L // 2)
                 if r.half_done == 2 * r.sweeps:
