@@ -171,13 +171,17 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_lj(const FillDesc d) {
 // streams of one request) and fills its streams one after the other.
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_batch_mlcg(const BatchQueue q) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  __shared__ FillDesc desc[WPB];
   for (;;) {
     const uint32_t it = pop_warp(q.counter);
     if (it >= q.n_items) break;
     const BatchItem I = q.items[it];
     const BatchReq& r = q.reqs[I.req];
-    const FillDesc& d = r.d;
+    FillDesc& d = desc[wi];
+    __syncwarp();
+    load_desc(&d, r.d, lane, 32);
+    __syncwarp();
     if (r.gen == GGL) {
       LjConst<GglLJ> K;
       K.init(lane, d.n_per);

@@ -169,12 +169,16 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
 template <int WPB, bool F32>
 __global__ void __launch_bounds__(WPB * 32) k_batch_mt(const BatchQueue q) {
   __shared__ __align__(16) uint32_t table[WPB][624];
+  __shared__ FillDesc desc[WPB];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   for (;;) {
     const uint32_t it = pop_warp(q.counter);
     if (it >= q.n_items) break;
     const BatchItem I = q.items[it];
-    const FillDesc& d = q.reqs[I.req].d;
+    FillDesc& d = desc[wi];
+    __syncwarp();
+    load_desc(&d, q.reqs[I.req].d, lane, 32);
+    __syncwarp();
     for (uint32_t k = 0; k < I.rows; k++) mt_stream<F32 ? OUT_F32 : OUT_U32>(d, I.row0 + k, table[wi], lane);
   }
 }

@@ -155,7 +155,10 @@ template <int T, bool F32>
 __global__ void __launch_bounds__(T) k_batch_ranmar(const BatchQueue q) {
   __shared__ uint32_t smem[(T / 32) * kRanmarRing];
   const BatchItem si = q.items[blockIdx.x];
-  ranmar_warps<T / 32, F32 ? OUT_F32 : OUT_U32, true>(q.reqs[si.req].d, si.row0, (int)si.rows, smem);
+  __shared__ FillDesc sd;
+  load_desc(&sd, q.reqs[si.req].d, threadIdx.x, T);
+  __syncthreads();
+  ranmar_warps<T / 32, F32 ? OUT_F32 : OUT_U32, true>(sd, si.row0, (int)si.rows, smem);
 }
 
 template <int T, bool F32>

@@ -196,7 +196,9 @@ __global__ void __launch_bounds__(T) k_batch_xor128(const BatchQueue q) {
     const uint32_t it = pop_cta(q.counter, &slot);
     if (it >= q.n_items) break;
     const BatchItem si = q.items[it];
-    const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
+    __shared__ FillDesc sd;
+    load_desc(&sd, q.reqs[si.req].d, threadIdx.x, T);
+    __syncthreads();
     simple_rows<Xor128Gen, T, K, S, F32 ? OUT_F32 : OUT_U32>(sd, si.row0, smem);
   }
 }
@@ -225,6 +227,7 @@ static cudaError_t launch_bx2(const BatchQueue& q, bool f32, cudaStream_t s) {
 
 cudaError_t launch_batch_xor128(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
   if (q.n_items == 0) return cudaSuccess;
+  if (t.threads == 64 && t.cols == 32 && t.stages == 1) return launch_bx2<64, 32, 1>(q, f32, s);
   if (t.threads == 128 && t.cols == 32 && t.stages == 2) return launch_bx2<128, 32, 2>(q, f32, s);
   if (t.threads == 128 && t.cols == 64 && t.stages == 1) return launch_bx2<128, 64, 1>(q, f32, s);
   if (t.threads == 256 && t.cols == 32 && t.stages == 1) return launch_bx2<256, 32, 1>(q, f32, s);

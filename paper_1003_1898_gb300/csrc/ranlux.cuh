@@ -309,7 +309,9 @@ __global__ void __launch_bounds__(T, 768 / T) k_batch_ranlux(const BatchQueue q)
     const uint32_t it = pop_cta(q.counter, &slot);
     if (it >= q.n_items) break;
     const BatchItem si = q.items[it];
-    const FillDesc& sd = q.reqs[si.req].d;  // read from global memory as needed
+    __shared__ FillDesc sd;
+    load_desc(&sd, q.reqs[si.req].d, threadIdx.x, T);
+    __syncthreads();
     ranlux_rows<T, KT, P, F32 ? OUT_F32 : OUT_U32, true>(sd, si.row0, smem);
   }
 }
@@ -360,6 +362,7 @@ cudaError_t ranlux_fill_p(const FillDesc& d, Tile t, cudaStream_t s) {
 
 template <int P>
 cudaError_t ranlux_batch_p(const BatchQueue& q, Tile t, bool f32, cudaStream_t s) {
+  if (t.threads == 32) return f32 ? launch_bl<32, 48, P, true>(q, s) : launch_bl<32, 48, P, false>(q, s);
   if (t.threads == 64) return f32 ? launch_bl<64, 48, P, true>(q, s) : launch_bl<64, 48, P, false>(q, s);
   return f32 ? launch_bl<128, 48, P, true>(q, s) : launch_bl<128, 48, P, false>(q, s);
 }

@@ -107,14 +107,17 @@ class Server:
             c.close()
 
     # ------------------------------------------------------------------ sizes
-    def _fill_shape(self, n):
-        per = -(-n // self.n_streams)
+    def fill_shape(self, n):
+        """Draws per stream and block size of a fill of n numbers: ceil(n /
+        n_streams) rounded up to a multiple of 4 (16-byte row starts, so the
+        kernels keep their vector stores); the first n are the output."""
+        per = 4 * -(-(-(-n // self.n_streams)) // 4)
         return per, self.n_streams * per
 
     def request_bytes(self, r: Request) -> int:
         """Device bytes a request holds while it runs (counted against the cap)."""
         if r.kind == "fill":
-            return 4 * self._fill_shape(r.n)[1]
+            return 4 * self.fill_shape(r.n)[1]
         return r.L * r.L + self.hpt * 2 * r.L * r.L   # int8 lattice + draws of hpt half-sweeps
 
     # ------------------------------------------------------------------ run
@@ -210,7 +213,7 @@ class Server:
                 self.mem_used += need
                 with torch.cuda.stream(self.stream):
                     if r.kind == "fill":
-                        per, total = self._fill_shape(r.n)
+                        per, total = self.fill_shape(r.n)
                         r.out = torch.empty(total, dtype=torch.float32 if r.f32 else torch.int32,
                                             device="cuda")
                         fills.append({"st": c.handle, "d_out": r.out, "n_per_stream": per,

@@ -30,12 +30,16 @@ BATCH_RANLUX_P = 223
 
 
 def request_split(gen: str, n: int):
-    """Streams and draws per stream of a request for n numbers: S = ceil(n /
-    C_g) streams, ceil(n / S) draws each; the first n of the stream-major
-    block are the request's output."""
+    """Streams and draws per stream of a request for n numbers: ceil(n /
+    C_g) streams would take ceil(n / S) draws each; that count is rounded up
+    to a multiple of 4 (so that every stream's row starts on a 16-byte
+    boundary and the kernels keep their vector stores) and S = ceil(n /
+    draws) streams are used.  The first n of the stream-major block are the
+    request's output."""
     c = DRAWS_PER_STREAM.get(gen, DEFAULT_DRAWS_PER_STREAM)
     s = -(-n // c)
-    return s, -(-n // s)
+    per = 4 * -(-(-(-n // s)) // 4)
+    return -(-n // per), per
 
 
 def batched_requests(n_requests: int = 20000, seed: int = 0xB47C, min_len: int = 100,

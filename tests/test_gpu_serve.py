@@ -56,7 +56,7 @@ def test_mix_equals_oracle_and_clients_alone(hpt):
         g, lux, seed = specs[r.client]
         skip = consumed.get(r.client, 0)
         if r.kind == "fill":
-            per = -(-r.n // NS)
+            per = srv.fill_shape(r.n)[0]
             ref = oracle.fill(g, seed, NS, per, luxury=lux, skip=skip).reshape(-1)[:r.n]
             if r.f32:
                 ref = oracle.to_f32(g, ref).view(np.uint32)
