@@ -242,7 +242,12 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
     }
 #pragma unroll
     for (int jj = 0; jj < 24; jj++) R[jj] = ring[(jj + h) % 24] << 8;  // h == 24 - pos0 here
-    flush();  // the head alone, so whole blocks start at tile column 0
+    // Flushes then come every 48 columns; they keep 64-byte-aligned row
+    // runs when the first one ends on a multiple of 16 columns.  So the head
+    // is flushed alone when h is a multiple of 16, and otherwise, when h = 8
+    // or 24, kept in the tile with the first block written after it (h is a
+    // multiple of 4, so the block's 16-byte shared stores stay aligned).
+    if (!((h & 3) == 0 && ((h + 24) & 15) == 0)) flush();
   } else {
 #pragma unroll
     for (int jj = 0; jj < 24; jj++) R[jj] = active ? d.state[jj * nr + row] << 8 : 0u;
@@ -250,7 +255,8 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   }
 
   // Whole blocks: discard p - 24, deliver 24, all in registers; each block
-  // is six 16-byte shared stores at tile column 0 or 24.
+  // is six 16-byte shared stores at tile column 0 or 24 (or right after a
+  // head of 8 or 24 kept in the tile).
   while (n - j >= 24) {
     discard_cycle<P>(R, c);
     if (fill + 24 > KT) flush();
