@@ -130,7 +130,10 @@ int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
 
 /* Single-sequence jump-ahead fill (GGL, RANECU, XOR128 and MT19937): write draws
  * 1..n of the one sequence started at x0 to d_out[0..n), computed as
- * n_chunks contiguous chunks in parallel, L = ceil(n / n_chunks) draws each.
+ * n_chunks contiguous chunks in parallel, L = ceil(n / n_chunks) draws each
+ * (GGL and RANECU on their thread-per-stream tile, and XOR128, cut the
+ * sequence into more, shorter chunks when n_chunks is too few to fill the
+ * GPU; the output is the same).
  * GGL: x0 in [1, 2^31-2], chunk c starts from a^(c*L) x0 mod m by
  * square-and-multiply (Appendix A, eq. MLCG).  RANECU: x0 = s1 | (s2 << 32)
  * with s1 in [1, m1-1], s2 in [1, m2-1], both components jumped separately.

@@ -4,6 +4,7 @@
 // bookkeeping of the positions that are uniform over a handle's streams
 // (RANLUX's place in its luxury block, MT19937's table index), and dispatch
 // to the kernels.  Every draw is produced on the GPU.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -86,7 +87,15 @@ int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, 
     const uint64_t s1 = x0 & 0xFFFFFFFFull, s2 = x0 >> 32;
     if (s1 == 0 || s1 >= 2147483563ull || s2 == 0 || s2 >= 2147483399ull) return PRNG_ESEED;
   }
-  const uint64_t L = (n + n_chunks - 1) / n_chunks;  // draws per chunk
+  // The generator's fill tile decides the kernel.  The lane-parallel one
+  // runs a warp per chunk as asked; the staged one runs a thread per chunk,
+  // so it cuts the sequence into more, shorter chunks when there are too
+  // few to fill the GPU (the output is the same sequence).
+  const Tile t = default_tile(gen, 0);
+  const bool lanes = t.cols == 128;
+  const uint64_t want = lanes ? n_chunks
+                              : std::max<uint64_t>(n_chunks, std::min<uint64_t>((n + 255) / 256, 131072));
+  const uint64_t L = (n + want - 1) / want;          // draws per chunk
   FillDesc d{};
   d.state = nullptr;
   d.n_rows = (n + L - 1) / L;                        // no empty chunk
@@ -97,9 +106,8 @@ int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, 
   d.x0 = x0;
   d.mode = f32 ? OUT_F32 : OUT_U32;
   d.jump = 1;
-  Tile t = default_tile(gen, 0);
-  if (t.cols != 128) t = Tile{256, 128, 1};  // jump chunks always run lane-parallel
-  if (launch_fill_mlcg(gen, d, t, s) != cudaSuccess) return PRNG_ECUDA;
+  const cudaError_t e = lanes ? launch_fill_mlcg(gen, d, t, s) : launch_fill_simple(gen, d, t, s);
+  if (e != cudaSuccess) return PRNG_ECUDA;
   return PRNG_OK;
 }
 

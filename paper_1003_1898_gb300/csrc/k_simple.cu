@@ -19,7 +19,12 @@ namespace prng {
 
 struct GglGen {
   static constexpr int SH = 7, WB = 31;
+  static constexpr bool JUMPS = true;
   uint32_t x;
+  // Row of a jump fill: x0 a^k mod m (Appendix A, eq. MLCG).
+  __device__ __forceinline__ void jump_start(uint64_t x0, uint64_t k) {
+    x = mulmod_pm<1u>(powmod_pm<1u>(16807u, k), (uint32_t)x0);
+  }
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) { x = st[row]; }
   __device__ __forceinline__ void store(uint32_t* st, uint64_t n, uint64_t row) const { st[row] = x; }
   __device__ __forceinline__ void zero() { x = 1; }
@@ -32,7 +37,13 @@ struct GglGen {
 
 struct RanecuGen {
   static constexpr int SH = 7, WB = 31;
+  static constexpr bool JUMPS = true;
   uint32_t s1, s2;
+  // Row of a jump fill: each component jumped separately from x0 = s1 | s2 << 32.
+  __device__ __forceinline__ void jump_start(uint64_t x0, uint64_t k) {
+    s1 = mulmod_pm<85u>(powmod_pm<85u>(40014u, k), (uint32_t)(x0 & 0xFFFFFFFFu));
+    s2 = mulmod_pm<249u>(powmod_pm<249u>(40692u, k), (uint32_t)(x0 >> 32));
+  }
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
     s1 = st[row];
     s2 = st[n + row];
@@ -56,6 +67,7 @@ struct RanecuGen {
 
 struct Xor128Gen {
   static constexpr int SH = 8, WB = 32;
+  static constexpr bool JUMPS = false;
   uint32_t x, y, z, w;
   __device__ __forceinline__ void load(const uint32_t* st, uint64_t n, uint64_t row) {
     x = st[row];
@@ -107,8 +119,14 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
   const bool active = row < d.n_rows;
 
   G g;
-  if (!active) g.zero();
-  else g.load(d.state, d.n_rows, row);
+  if (!active) {
+    g.zero();
+  } else if constexpr (G::JUMPS) {
+    if (d.jump) g.jump_start(d.x0, row * d.pitch);   // chunk `row` of one sequence
+    else g.load(d.state, d.n_rows, row);
+  } else {
+    g.load(d.state, d.n_rows, row);
+  }
 
   uint32_t* out = static_cast<uint32_t*>(d.out);
   const bool vec_ok = ((d.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
@@ -178,7 +196,7 @@ __device__ __forceinline__ void simple_rows(const FillDesc& d, uint64_t row0, ui
     if constexpr (S == 1) __syncthreads();
     else buf ^= 1;
   }
-  if (active) g.store(d.state, d.n_rows, row);
+  if (active && !d.jump) g.store(d.state, d.n_rows, row);
 }
 
 template <class G, int T, int K, int S, int OM>
