@@ -11,7 +11,9 @@
  *     (prng_strerror() names it).  Arguments are validated on the host
  *     before anything is launched; a rejected call changes nothing.
  *   - Pointers named d_* are CUDA device pointers owned by the caller; the
- *     library never frees them.  Host pointers are named h_*.
+ *     library never frees them.  Host pointers are named h_*.  An output
+ *     d_* may also be host memory from prng_host_alloc (written over the
+ *     host link).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Fills are asynchronous on that stream; the caller orders
  *     work on one handle (a handle is not thread-safe).
@@ -296,6 +298,20 @@ int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t co
                   uint32_t stages);
 int prng_get_tile(prng_gen_t gen, uint32_t luxury, uint32_t *threads, uint32_t *cols,
                   uint32_t *stages);
+
+/* Host output buffers.  prng_host_alloc returns `bytes` of page-locked host
+ * memory mapped into the device's address space at the same address
+ * (unified addressing), so that the pointer can be passed as the d_out of
+ * any fill, jump fill or batched request: the kernels then store the
+ * numbers straight into host memory over the host link (NVLink-C2C on
+ * Grace-Blackwell), with no device staging buffer and no copy.  The caller
+ * owns the memory and reads it after the fill's stream has been
+ * synchronised.  PRNG_ENULL if h_out is NULL, PRNG_ESIZE for bytes = 0,
+ * PRNG_EALLOC if the allocation fails, PRNG_ECUDA if the device address
+ * differs from the host address (no unified addressing; nothing is kept).
+ * prng_host_free accepts NULL and only pointers from prng_host_alloc. */
+int prng_host_alloc(void **h_out, size_t bytes);
+int prng_host_free(void *h_buf);
 
 /* Handle properties (any pointer may be NULL). */
 int prng_info(const prng_state *st, int32_t *gen, int32_t *p, uint32_t *n_streams,

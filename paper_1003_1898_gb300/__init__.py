@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
         "prng_ising_fused": ([vp, vp, u32, u32, u32, u32, vp], ctypes.c_int),
         "prng_ising_thresholds": ([ctypes.c_double, ctypes.POINTER(u32), ctypes.POINTER(u32)],
                                   ctypes.c_int),
+        "prng_host_alloc": ([ctypes.POINTER(vp), ctypes.c_size_t], ctypes.c_int),
+        "prng_host_free": ([vp], ctypes.c_int),
         "prng_destroy": ([vp], None),
         "prng_strerror": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -291,6 +293,51 @@ def prng_ising_fused(h, spins, L: int, colour: int, t4: int, t8: int, stream=Non
     where they are made (no draw buffer)."""
     _check(lib().prng_ising_fused(h, _ptr(spins), L, colour, t4, t8, _stream(stream)),
            "prng_ising_fused")
+
+
+def prng_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory mapped at the same device address: fills given
+    this pointer store their numbers straight into host memory."""
+    p = ctypes.c_void_p()
+    _check(lib().prng_host_alloc(ctypes.byref(p), nbytes), "prng_host_alloc")
+    return p.value
+
+
+def prng_host_free(ptr):
+    _check(lib().prng_host_free(ptr), "prng_host_free")
+
+
+class HostBuffer:
+    """Host output buffer from prng_host_alloc: pass ``.ptr`` (or the buffer
+    itself) as a fill's output; read it through ``.numpy(dtype)`` after the
+    fill's stream has been synchronised."""
+
+    def __init__(self, nbytes: int):
+        self.nbytes = int(nbytes)
+        self.ptr = prng_host_alloc(self.nbytes)
+
+    def data_ptr(self) -> int:
+        return self.ptr
+
+    def numpy(self, dtype="uint32", count: int | None = None):
+        import numpy as np
+        dt = np.dtype(dtype)
+        n = self.nbytes // dt.itemsize if count is None else int(count)
+        if n * dt.itemsize > self.nbytes:
+            raise ValueError("view larger than the buffer")
+        raw = (ctypes.c_char * (n * dt.itemsize)).from_address(self.ptr)
+        return np.frombuffer(raw, dtype=dt, count=n)
+
+    def close(self):
+        if self.ptr:
+            prng_host_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def prng_destroy(h):

@@ -418,6 +418,29 @@ int prng_info(const prng_state* st, int32_t* gen, int32_t* p, uint32_t* n_stream
   return PRNG_OK;
 }
 
+int prng_host_alloc(void** h_out, size_t bytes) {
+  if (h_out == nullptr) return PRNG_ENULL;
+  if (bytes == 0) return PRNG_ESIZE;
+  void* h = nullptr;
+  if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return PRNG_EALLOC;
+  }
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess || d != h) {
+    cudaGetLastError();
+    cudaFreeHost(h);
+    return PRNG_ECUDA;
+  }
+  *h_out = h;
+  return PRNG_OK;
+}
+
+int prng_host_free(void* h_buf) {
+  if (h_buf == nullptr) return PRNG_OK;
+  return cudaFreeHost(h_buf) == cudaSuccess ? PRNG_OK : PRNG_ECUDA;
+}
+
 void prng_destroy(prng_state* st) {
   if (st == nullptr) return;
   if (st->d_state) cudaFree(st->d_state);
@@ -428,10 +451,10 @@ const char* prng_strerror(int code) {
   switch (code) {
     case PRNG_OK: return "success";
     case PRNG_EGEN: return "unknown generator";
-    case PRNG_ELUXURY: return "RANLUX luxury must be 0..4 or one of 24, 48, 97, 223, 389";
+    case PRNG_ELUXURY: return "RANLUX luxury must be 0..4 or one of 24, 48, 97, 223, 389, 120, 240, 408";
     case PRNG_ESIZE: return "invalid size or alignment";
     case PRNG_ENULL: return "required pointer is NULL";
-    case PRNG_EALLOC: return "device allocation failed";
+    case PRNG_EALLOC: return "device or host allocation failed";
     case PRNG_ECUDA: return "CUDA call or kernel launch failed";
     case PRNG_EUNSUPPORTED: return "operation not supported for this generator";
     case PRNG_EBLOB: return "state blob does not match this handle";

@@ -73,8 +73,16 @@ def test_null_handles(L):
     L.prng_destroy(None)
 
 
+def test_host_alloc_rejects_bad_arguments(L):
+    p = ctypes.c_void_p()
+    assert L.prng_host_alloc(None, 64) == -4
+    assert L.prng_host_alloc(ctypes.byref(p), 0) == -3
+    assert p.value is None
+    assert L.prng_host_free(None) == 0
+
+
 def test_strerror_names_every_code(L):
-    for code in range(0, -10, -1):
+    for code in range(0, -12, -1):
         s = P.prng_strerror(code)
         assert s and s != "unknown error code"
     assert P.prng_strerror(-99) == "unknown error code"
