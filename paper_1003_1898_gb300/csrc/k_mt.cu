@@ -187,89 +187,132 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_mt(const BatchQueue q) {
 // g(T) applied to row r - src_off and moved one more word on, where T moves
 // a table one word along the sequence of Appendix A, "Mersenne twister".
 // Word j of the result is the XOR, over the coefficients g_i = 1, of word
-// 1 + i + j of the word sequence that the source table starts.  One warp
-// per row walks that sequence 624 words at a time: the current table and
-// the next (twisted from a copy) sit side by side in shared memory, so the
-// words 1 + i + j of a block of 624 values of i are one contiguous window.
-// Lane l owns result words 20 l .. 20 l + 19 in registers and takes four
-// coefficients at a time: the 23 words they need start one word past a
-// 16-byte boundary (i is a multiple of 4 and 1 + i + 20 l = 1 mod 4), so they
-// are seven aligned 16-byte shared loads (lanes 80 bytes apart hit eight
-// different bank quads), and the set coefficients among the four (BITS, a
-// compile-time variant) are folded with three-input XORs.
-template <int BITS>
-__device__ __forceinline__ void mt_poly_quad(uint32_t (&acc)[20], const uint32_t* B, int a) {
-  uint32_t win[28];
-#pragma unroll
-  for (int q = 0; q < 7; q++) {
-    const uint4 v = *reinterpret_cast<const uint4*>(B + a + 4 * q);
-    win[4 * q] = v.x; win[4 * q + 1] = v.y; win[4 * q + 2] = v.z; win[4 * q + 3] = v.w;
-  }
+// 1 + i + j of the word sequence that the source table starts.  A warp
+// walks that sequence 624 words at a time: the current table and the next
+// (twisted from a copy) sit side by side in shared memory, so the words
+// 1 + i + j of a block of 624 values of i are one contiguous window.  Lane l
+// owns result words 20 l .. 20 l + 19 in registers and takes sixteen
+// coefficients at a time: the 35 words they need start one word past a
+// 16-byte boundary (i is a multiple of 16 and 1 + i + 20 l = 1 mod 4), so
+// they are ten aligned 16-byte shared loads (lanes 80 bytes apart hit eight
+// different bank quads), shared by the sixteen coefficients.  Each nibble
+// of set coefficients (BITS, a compile-time variant) is folded with
+// three-input XORs.
+//
+// The 19937 coefficients are 32 blocks of 624.  A table's blocks can be
+// split over S warps (segments of ceil(32 / S) blocks): segment s first
+// twists its copy of the source table forward by its first block, then
+// accumulates its blocks and XORs its partial result into the (zeroed)
+// destination row with atomics.  S = 1 stores the result directly and may
+// run in place (destination row = source row).
+template <int OFF, int BITS>
+__device__ __forceinline__ void mt_poly_nib(uint32_t (&acc)[20], const uint32_t (&win)[40]) {
 #pragma unroll
   for (int t = 0; t < 20; t++) {
     uint32_t x = acc[t];
-    if (BITS & 1) x ^= win[1 + t];
-    if (BITS & 2) x ^= win[2 + t];
-    if (BITS & 4) x ^= win[3 + t];
-    if (BITS & 8) x ^= win[4 + t];
+    if (BITS & 1) x ^= win[OFF + 1 + t];
+    if (BITS & 2) x ^= win[OFF + 2 + t];
+    if (BITS & 4) x ^= win[OFF + 3 + t];
+    if (BITS & 8) x ^= win[OFF + 4 + t];
     acc[t] = x;
+  }
+}
+
+template <int OFF>
+__device__ __forceinline__ void mt_poly_nib_any(uint32_t bits4, uint32_t (&acc)[20],
+                                                const uint32_t (&win)[40]) {
+  switch (bits4) {
+#define PRNG_MT_NIB(b) case b: mt_poly_nib<OFF, b>(acc, win); break;
+    PRNG_MT_NIB(1) PRNG_MT_NIB(2) PRNG_MT_NIB(3) PRNG_MT_NIB(4) PRNG_MT_NIB(5)
+    PRNG_MT_NIB(6) PRNG_MT_NIB(7) PRNG_MT_NIB(8) PRNG_MT_NIB(9) PRNG_MT_NIB(10)
+    PRNG_MT_NIB(11) PRNG_MT_NIB(12) PRNG_MT_NIB(13) PRNG_MT_NIB(14) PRNG_MT_NIB(15)
+#undef PRNG_MT_NIB
+    default: break;
   }
 }
 
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_mt_poly_apply(const __grid_constant__ MtPoly g,
                                                             uint32_t* state, uint64_t r0,
-                                                            uint64_t r1, uint64_t src_off) {
-  constexpr int D = 19937;
+                                                            uint64_t r1, uint64_t src_off,
+                                                            uint32_t S) {
+  constexpr int D = 19937, NB = (D + 623) / 624;
   // current table | next table | room for lane 31's over-reach (its words
-  // past 623 are computed and dropped)
+  // past 623 are computed and dropped; its last window ends at word 1267)
   __shared__ __align__(16) uint32_t buf[WPB][1280];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const uint64_t r = r0 + (uint64_t)blockIdx.x * WPB + wi;
+  const uint64_t w = (uint64_t)blockIdx.x * WPB + wi;
+  const uint64_t r = r0 + w / S;
   if (r >= r1) return;  // whole warp; no CTA-wide barriers below
+  const int per = (NB + (int)S - 1) / (int)S;
+  const int b0 = (int)(w % S) * per, b1 = b0 + per < NB ? b0 + per : NB;
+  if (b0 >= b1) return;
   uint32_t* B = buf[wi];
   const uint32_t* src = state + (r - src_off) * 624;
   for (int k = lane; k < 624; k += 32) B[k] = src[k];
   for (int k = 1248 + lane; k < 1280; k += 32) B[k] = 0;
+  for (int b = 0; b < b0; b++) {   // to the segment's first block
+    __syncwarp();
+    mt_twist<OUT_U32, false>(B, lane, nullptr, 624, false);
+  }
   uint32_t acc[20];
 #pragma unroll
   for (int t = 0; t < 20; t++) acc[t] = 0;
-  for (int i0 = 0; i0 < D; i0 += 624) {
+  for (int i0 = b0 * 624; i0 < b1 * 624 && i0 < D; i0 += 624) {
     __syncwarp();
     for (int k = lane; k < 624; k += 32) B[624 + k] = B[k];
     __syncwarp();
     mt_twist<OUT_U32, false>(B + 624, lane, nullptr, 624, false);  // the next 624 words
     const int i1 = i0 + 624 < D ? i0 + 624 : D;
-    for (int i = i0; i < i1; i += 4) {   // i0 and i are multiples of 4: four bits of one word
-      uint32_t bits4 = (g.w[i >> 5] >> (i & 31)) & 0xFu;
-      if (i1 - i < 4) bits4 &= (1u << (i1 - i)) - 1u;
-      if (!bits4) continue;
+    for (int i = i0; i < i1; i += 16) {   // i0 and i are multiples of 16: half of one word
+      uint32_t bits = (g.w[i >> 5] >> (i & 31)) & 0xFFFFu;
+      if (i1 - i < 16) bits &= (1u << (i1 - i)) - 1u;
+      if (!bits) continue;
       const int a = (i - i0) + 20 * lane;          // 16-byte aligned; the window starts at a + 1
-      switch (bits4) {
-#define PRNG_MT_QUAD(b) case b: mt_poly_quad<b>(acc, B, a); break;
-        PRNG_MT_QUAD(1) PRNG_MT_QUAD(2) PRNG_MT_QUAD(3) PRNG_MT_QUAD(4) PRNG_MT_QUAD(5)
-        PRNG_MT_QUAD(6) PRNG_MT_QUAD(7) PRNG_MT_QUAD(8) PRNG_MT_QUAD(9) PRNG_MT_QUAD(10)
-        PRNG_MT_QUAD(11) PRNG_MT_QUAD(12) PRNG_MT_QUAD(13) PRNG_MT_QUAD(14) PRNG_MT_QUAD(15)
-#undef PRNG_MT_QUAD
-        default: break;
+      uint32_t win[40];
+#pragma unroll
+      for (int q = 0; q < 10; q++) {
+        const uint4 v = *reinterpret_cast<const uint4*>(B + a + 4 * q);
+        win[4 * q] = v.x; win[4 * q + 1] = v.y; win[4 * q + 2] = v.z; win[4 * q + 3] = v.w;
       }
+      mt_poly_nib_any<0>(bits & 0xFu, acc, win);
+      mt_poly_nib_any<4>((bits >> 4) & 0xFu, acc, win);
+      mt_poly_nib_any<8>((bits >> 8) & 0xFu, acc, win);
+      mt_poly_nib_any<12>(bits >> 12, acc, win);
     }
     __syncwarp();
     for (int k = lane; k < 624; k += 32) B[k] = B[624 + k];
   }
   uint32_t* dst = state + r * 624;
+  if (S == 1) {
 #pragma unroll
-  for (int t = 0; t < 20; t++)
-    if (20 * lane + t < 624) dst[20 * lane + t] = acc[t];
+    for (int t = 0; t < 20; t++)
+      if (20 * lane + t < 624) dst[20 * lane + t] = acc[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < 20; t++)
+      if (20 * lane + t < 624) atomicXor(dst + 20 * lane + t, acc[t]);
+  }
 }
 
 cudaError_t launch_mt_poly_apply(const MtPoly& g, uint32_t* state, uint64_t r0, uint64_t r1,
                                  uint64_t src_off, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
   constexpr int WPB = 4;
-  const uint64_t blocks = (r1 - r0 + WPB - 1) / WPB;
+  // Few tables: split each table's coefficient blocks over up to 32 warps
+  // (destination rows zeroed first), so that a pass keeps about 4096 warps
+  // busy.  In place (src_off = 0) needs the unsplit form.
+  const uint64_t tables = r1 - r0;
+  uint32_t S = 1;
+  if (src_off != 0)
+    while (S < 32 && tables * S < 4096) S *= 2;
+  if (S > 1) {
+    const cudaError_t e = cudaMemsetAsync(state + r0 * 624, 0, tables * 624 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  const uint64_t blocks = (tables * S + WPB - 1) / WPB;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  k_mt_poly_apply<WPB><<<(unsigned)blocks, WPB * 32, 0, s>>>(g, state, r0, r1, src_off);
+  k_mt_poly_apply<WPB><<<(unsigned)blocks, WPB * 32, 0, s>>>(g, state, r0, r1, src_off, S);
   return cudaGetLastError();
 }
 

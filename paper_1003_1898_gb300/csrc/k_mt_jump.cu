@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -137,6 +138,28 @@ void reduce(uint64_t* r, int top) {
   }
 }
 
+// r = g^2 mod phi, times t (mod phi) when times_t; g and r have kW words.
+void square_mod(const uint64_t* g, uint64_t* r, bool times_t) {
+  std::fill(r, r + kW, 0ull);
+  for (int w = 0; w <= (kD - 1) / 64; w++) {    // square: coefficient i -> 2 i
+    for (int half = 0; half < 2; half++) {
+      uint64_t x = (g[w] >> (32 * half)) & 0xFFFFFFFFull;
+      x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+      x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+      x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+      x = (x | (x << 2)) & 0x3333333333333333ull;
+      x = (x | (x << 1)) & 0x5555555555555555ull;
+      r[2 * w + half] = x;
+    }
+  }
+  reduce(r, 2 * kD - 2);
+  if (times_t) {
+    for (int w = kW - 1; w > 0; w--) r[w] = (r[w] << 1) | (r[w - 1] >> 63);
+    r[0] <<= 1;
+    reduce(r, kD);
+  }
+}
+
 // t^e mod phi as a packed polynomial of kW words.
 void pow_t(uint64_t e, uint64_t* g) {
   std::fill(g, g + kW, 0ull);
@@ -145,41 +168,37 @@ void pow_t(uint64_t e, uint64_t* g) {
   while (b >= 0 && !((e >> b) & 1)) b--;
   std::vector<uint64_t> r(kW);
   for (; b >= 0; b--) {
-    std::fill(r.begin(), r.end(), 0ull);
-    for (int w = 0; w <= (kD - 1) / 64; w++) {    // square: coefficient i -> 2 i
-      for (int half = 0; half < 2; half++) {
-        uint64_t x = (g[w] >> (32 * half)) & 0xFFFFFFFFull;
-        x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
-        x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
-        x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
-        x = (x | (x << 2)) & 0x3333333333333333ull;
-        x = (x | (x << 1)) & 0x5555555555555555ull;
-        r[2 * w + half] = x;
-      }
-    }
-    reduce(r.data(), 2 * kD - 2);
-    if ((e >> b) & 1) {                            // times t
-      for (int w = kW - 1; w > 0; w--) r[w] = (r[w] << 1) | (r[w - 1] >> 63);
-      r[0] <<= 1;
-      reduce(r.data(), kD);
-    }
+    square_mod(g, r.data(), (e >> b) & 1);
     std::copy(r.begin(), r.end(), g);
   }
 }
 
-// The device form of t^(k-1) mod phi, k >= 1; the last one is kept.
+MtPoly device_form(const uint64_t* g) {
+  MtPoly p;
+  for (int i = 0; i < 624; i++) p.w[i] = (uint32_t)(g[i / 2] >> (32 * (i & 1)));
+  return p;
+}
+
+// The device form of t^(k-1) mod phi, k >= 1, from a bounded cache (a jump
+// fill needs one polynomial per doubling pass).  A miss whose k is even and
+// whose k / 2 is cached takes one squaring: t^(k-1) = t (t^(k/2-1))^2.
 MtPoly jump_poly(uint64_t k) {
   static std::mutex lock;
-  static uint64_t cached_k = 0;
-  static MtPoly cached;
+  static std::unordered_map<uint64_t, MtPoly> cache;
   std::lock_guard<std::mutex> guard(lock);
-  if (k != cached_k) {
-    std::vector<uint64_t> g(kW);
+  auto it = cache.find(k);
+  if (it != cache.end()) return it->second;
+  std::vector<uint64_t> g(kW, 0ull);
+  auto half = (k % 2 == 0) ? cache.find(k / 2) : cache.end();
+  if (half != cache.end()) {
+    std::vector<uint64_t> h(kW, 0ull);
+    for (int i = 0; i < 624; i++) h[i / 2] |= (uint64_t)half->second.w[i] << (32 * (i & 1));
+    square_mod(h.data(), g.data(), true);
+  } else {
     pow_t(k - 1, g.data());
-    for (int i = 0; i < 624; i++) cached.w[i] = (uint32_t)(g[i / 2] >> (32 * (i & 1)));
-    cached_k = k;
   }
-  return cached;
+  if (cache.size() >= 256) cache.clear();
+  return cache.emplace(k, device_form(g.data())).first->second;
 }
 
 }  // namespace
