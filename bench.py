@@ -179,6 +179,70 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """The same record read through NVML (read-only queries: current and
+    maximum SM clock, active clock-event reasons) every 5 ms, so that a
+    timed region of a few tens of milliseconds still gets several samples.
+    The device is found by its UUID."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str):
+        import ctypes
+        self.ct = ctypes
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("NVML has no device with this UUID")
+        try:
+            self.get_reasons = self.nv.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.get_reasons = self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 \
+            else None
+        self.samples = []
+        self.stop = threading.Event()
+
+    def _loop(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0 and \
+                    self.get_reasons(self.h, ct.byref(rs)) == 0:
+                self.samples.append((float(mhz.value), int(rs.value)))
+            time.sleep(0.005)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=5)
+        self.nv.nvmlShutdown()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "source": "nvml"}
+        reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml"}
+
+
+def clock_sampler(torch, dev, local_rank):
+    """NVML sampling when the driver's library is there, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(str(torch.cuda.get_device_properties(dev).uuid))
+    except Exception:
+        return ClockSampler(local_rank)
+
+
 # ------------------------------------------------------------------ oracle arm
 
 def cpu_oracle_rate(sample_per_item: int):
@@ -231,6 +295,21 @@ def cpu_oracle_rate_threads(sample_per_item: int, threads: int):
             t_total += dt * (numbers / (per * threads))
             n_total += numbers
     return n_total / t_total
+
+
+def rank_seed_base(g: str, rank: int) -> int:
+    """Rank `rank` owns streams [rank n, (rank + 1) n) of one handle of
+    world * n streams (n = this generator's stream count): stream i of a
+    handle is seeded from base + i, so its base is SEED + rank * n."""
+    return SEED + rank * shape(g)[0]
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (all-reduce MAX; a CUDA tensor under NCCL)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_reference(args, rank, world):
@@ -422,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
     sid = stream.cuda_stream
 
     # Each rank owns disjoint streams: seed bases offset by the stream count.
-    seed_r = {g: SEED + rank * shape(g)[0] for g in GENS}
+    seed_r = {g: rank_seed_base(g, rank) for g in GENS}
     handles = {g: P.prng_create(g, seed_r[g], shape(g)[0], RANLUX_P if g == "ranlux" else 0)
                for g in GENS}
     out_u = torch.empty(N_STREAMS * N_PER, dtype=torch.int32, device=dev)
@@ -456,7 +535,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
+    with clock_sampler(torch, dev, local_rank) as clk:
         t0.record(stream)
         for _ in range(args.steps):
             one_step(True)
@@ -467,9 +546,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms_total = t0.elapsed_time(t1)
     if world > 1:
-        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+        ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
     value = world * numbers_per_step() / (ms_step / 1e3)
     launches_per_step = len(GENS) + len(items)
