@@ -166,7 +166,7 @@ __device__ __forceinline__ uint32_t lux_conv(uint32_t x) {
 template <int P>
 __device__ __forceinline__ void discard_cycle(uint32_t (&R)[24], uint32_t& c) {
   constexpr int D = P - 24, Q = D / 24, RR = D % 24;
-#pragma unroll 1
+#pragma unroll
   for (int g = 0; g < Q; g++) swb24(R, c);
   swb_head<RR>(R, c);
   if constexpr (RR != 0) rotate_fixed(R, RR);
