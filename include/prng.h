@@ -291,7 +291,8 @@ int prng_batch_fill_noalloc(const prng_fill_req *reqs, uint32_t n_reqs, void *st
 
 /* Launch tile used by fills of generator `gen` (for RANLUX: of luxury p)
  * on this process: threads per CTA, staged draws per thread per tile
- * (RANMAR: 97, MT19937: 624) and staging buffers (1 or 2).  Set by the
+ * (RANMAR: 97, MT19937: 624) and staging buffers (1 or 2; for MT19937 the
+ * streams per warp: 1, or 2 on half a warp each).  Set by the
  * autotuner; only the combinations compiled into the library are accepted
  * (PRNG_EUNSUPPORTED otherwise).  Not thread-safe against concurrent fills. */
 int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t cols,

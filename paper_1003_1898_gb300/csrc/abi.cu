@@ -121,13 +121,14 @@ bool tile_supported(int gen, Tile t) {
   static const Tile mlcg[] = {{128, 128, 1}, {256, 128, 1}};
   static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1}};
   static const Tile mar[] = {{128, 128, 1}, {256, 128, 1}};
-  static const Tile mt[] = {{64, 624, 1}, {128, 624, 1}, {256, 624, 1}};
+  static const Tile mt[] = {{64, 624, 1}, {128, 624, 1}, {256, 624, 1},
+                            {32, 624, 2}, {64, 624, 2}, {128, 624, 2}, {256, 624, 2}};
   const Tile* list = simple;
   int n = 4;
   if ((gen == GGL || gen == RANECU) && t.cols == 128) { list = mlcg; n = 2; }
   else if (gen == RANLUX) { list = lux; n = 3; }
   else if (gen == RANMAR) { list = mar; n = 2; }
-  else if (gen == MT19937) { list = mt; n = 3; }
+  else if (gen == MT19937) { list = mt; n = 7; }
   for (int i = 0; i < n; i++)
     if (list[i].threads == t.threads && list[i].cols == t.cols && list[i].stages == t.stages)
       return true;

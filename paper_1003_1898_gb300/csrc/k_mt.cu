@@ -36,19 +36,24 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
   return f ^ (y >> 1) ^ ((0u - (y & 1u)) & 0x9908B0DFu);
 }
 
-// One twist of the warp's table (Appendix A, "Mersenne twister"), in place,
-// in five chunks of 128 entries; lane l owns entries k .. k+3, k = k0 + 4 l,
-// read and written with 16-byte shared accesses.  The lag X_{k+397} is old
+// One twist of a stream's table (Appendix A, "Mersenne twister"), in place,
+// by the LPS lanes that own the stream (32: a warp; 16: half a warp, the
+// warp's other half twisting another stream in step), in chunks of 4 LPS
+// entries (five of 128 or ten of 64); lane u owns entries k .. k+3,
+// k = k0 + 4 u, read and written with 16-byte shared accesses.  Any chunk
+// size up to 227 keeps the in-place order valid.  The lag X_{k+397} is old
 // for k < 227 and already replaced (X_{k-227}) from 227 on; both start one
 // word past a 16-byte boundary, so they come from two aligned 16-byte loads.
 // Only the lane holding k = 224..227 straddles the switch.  Each new word is
 // tempered and, if o != null, written to o[k] (16-byte stores when VEC);
 // PARTIAL: only entries k < take are written.
-template <int OM, bool PARTIAL>
+template <int OM, bool PARTIAL, int LPS = 32>
 __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec,
                                          const FillDesc* d = nullptr, uint64_t e0 = 0) {
+  constexpr int CH = 4 * LPS;
+  static_assert(CH <= 227, "a chunk may not reach its own lags");
 #pragma unroll
-  for (int k0 = 0; k0 < 640; k0 += 128) {
+  for (int k0 = 0; k0 < 624; k0 += CH) {
     const int k = k0 + 4 * lane;
     const bool valid = k < 624;
     uint4 a = make_uint4(0, 0, 0, 0), f = a;
@@ -56,7 +61,7 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
     if (valid) {
       a = *reinterpret_cast<const uint4*>(s + k);
       b = s[k + 4 == 624 ? 0 : k + 4];
-      const bool old_lag = (k0 + 128 <= 227) || (k0 < 227 && k + 3 < 227);
+      const bool old_lag = (k0 + CH <= 227) || (k0 < 227 && k + 3 < 227);
       const bool new_lag = (k0 >= 227) || k >= 227;
       if (old_lag || new_lag) {
         const int base = old_lag ? k + 396 : k - 228;
@@ -109,15 +114,22 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
   }
 }
 
-// Stream `row` of a fill by one warp; s is the warp's 624-word table.
-template <int OM>
-__device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane) {
+// Stream `row` of a fill by the LPS lanes that own it (lane u of them); s
+// is its 624-word table.  With LPS = 16 the two halves of a warp run two
+// streams in step: every branch that holds a __syncwarp is taken by the
+// whole warp (a 624-word block is twisted as partial or unaligned if either
+// stream needs it), and a half whose row is past the end (inactive) runs
+// along without touching memory outside shared memory.
+template <int OM, int LPS = 32>
+__device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane,
+                                          bool active = true) {
   uint32_t* gs = d.state + row * 624;
-  for (int k = lane; k < 624; k += 32) s[k] = gs[k];
+  if (active)
+    for (int k = lane; k < 624; k += LPS) s[k] = gs[k];
   __syncwarp();
 
   uint32_t* out = static_cast<uint32_t*>(d.out);
-  const bool store = out != nullptr;
+  const bool store = active && out != nullptr;
   uint32_t* orow = store ? out + row * d.pitch : nullptr;
   const uint64_t n = d.n_per;
   // Draws of this row that are written (all n unless the element limit cuts
@@ -129,7 +141,7 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
   if (mti < 624 && n > 0) {  // rest of the current table
     const uint64_t h = (624 - mti) < n ? (624 - mti) : n;
     if (store)
-      for (uint64_t k = lane; k < h && k < nv; k += 32)
+      for (uint64_t k = lane; k < h && k < nv; k += LPS)
         if constexpr (OM == OUT_F64) {
           if ((k & 1) == 0) st_pair<32>(orow + k, mt_temper(s[mti + k]), mt_temper(s[mti + k + 1]));
         } else {
@@ -138,30 +150,41 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
     j = h;
   }
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
-  const bool vec = store && ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
+  bool vec = !store || ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
+  if (LPS < 32) vec = __all_sync(0xFFFFFFFFu, vec);
   while (n - j >= 624) {
-    if (j + 624 <= nv)
-      mt_twist<OM, false>(s, lane, store ? orow + j : nullptr, 624, vec, &d, row * d.pitch + j);
+    bool whole = !store || j + 624 <= nv;
+    if (LPS < 32) whole = __all_sync(0xFFFFFFFFu, whole);
+    if (whole)
+      mt_twist<OM, false, LPS>(s, lane, store ? orow + j : nullptr, 624, vec, &d, row * d.pitch + j);
     else
-      mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)(nv > j ? nv - j : 0), false, &d,
-                         row * d.pitch + j);
+      mt_twist<OM, true, LPS>(s, lane, store ? orow + j : nullptr,
+                              (int)(store && nv > j ? (nv - j < 624 ? nv - j : 624) : 0), false, &d,
+                              row * d.pitch + j);
     j += 624;
   }
   if (j < n) {
-    const uint64_t take = nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
-    mt_twist<OM, true>(s, lane, store ? orow + j : nullptr, (int)take, false, &d, row * d.pitch + j);
+    const uint64_t take = store && nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
+    mt_twist<OM, true, LPS>(s, lane, store ? orow + j : nullptr, (int)take, false, &d, row * d.pitch + j);
   }
-  for (int k = lane; k < 624; k += 32) gs[k] = s[k];
+  if (active)
+    for (int k = lane; k < 624; k += LPS) gs[k] = s[k];
   __syncwarp();
 }
 
-template <int WPB, int OM>
+// SPW streams per warp (1: a warp per stream; 2: a half-warp each, which
+// halves the warps of a fill so that every stream of a large handle is
+// resident in one wave).
+template <int WPB, int OM, int SPW>
 __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
-  __shared__ __align__(16) uint32_t table[WPB][624];
+  __shared__ __align__(16) uint32_t table[WPB * SPW][624];
+  constexpr int LPS = 32 / SPW;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const uint64_t row = (uint64_t)blockIdx.x * WPB + wi;
-  if (row >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
-  mt_stream<OM>(d, row, table[wi], lane);
+  const int half = lane / LPS;
+  const uint64_t row0 = ((uint64_t)blockIdx.x * WPB + wi) * SPW;
+  if (row0 >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
+  const uint64_t row = row0 + half;
+  mt_stream<OM, LPS>(d, row, table[wi * SPW + half], lane % LPS, row < d.n_rows);
 }
 
 // Batched MT19937 fills: each warp pops an item (up to 2 streams of one
@@ -327,20 +350,29 @@ cudaError_t launch_batch_mt(const BatchQueue& q, Tile t, bool f32, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <int WPB, int OM>
+template <int WPB, int OM, int SPW>
 static cudaError_t launch_mt(const FillDesc& d, cudaStream_t s) {
-  const uint64_t grid = (d.n_rows + WPB - 1) / WPB;
-  k_fill_mt<WPB, OM><<<(unsigned)grid, WPB * 32, 0, s>>>(d);
+  const uint64_t grid = (d.n_rows + WPB * SPW - 1) / (WPB * SPW);
+  k_fill_mt<WPB, OM, SPW><<<(unsigned)grid, WPB * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 
+// Tile: threads per CTA (64, 128, 256; 32 with two streams per warp, so that
+// the CTAs of a large fill spread evenly over the SMs) and, in `stages`,
+// streams per warp.
 cudaError_t launch_fill_mt(const FillDesc& d, Tile t, cudaStream_t s) {
   if (d.n_rows == 0 || d.n_per == 0) return cudaSuccess;
   return with_mode(d.mode, [&](auto m) {
     constexpr int OM = decltype(m)::value;
-    if (t.threads == 64) return launch_mt<2, OM>(d, s);
-    if (t.threads == 256) return launch_mt<8, OM>(d, s);
-    return launch_mt<4, OM>(d, s);
+    if (t.stages == 2) {
+      if (t.threads == 32) return launch_mt<1, OM, 2>(d, s);
+      if (t.threads == 64) return launch_mt<2, OM, 2>(d, s);
+      if (t.threads == 256) return launch_mt<8, OM, 2>(d, s);
+      return launch_mt<4, OM, 2>(d, s);
+    }
+    if (t.threads == 64) return launch_mt<2, OM, 1>(d, s);
+    if (t.threads == 256) return launch_mt<8, OM, 1>(d, s);
+    return launch_mt<4, OM, 1>(d, s);
   });
 }
 

@@ -30,7 +30,7 @@ def test_tile_parity(gen, tile):
     saved = P.prng_get_tile(gen, lux)
     P.prng_set_tile(gen, lux, *tile)
     try:
-        ns = 300                                   # > 2 CTAs of 128, ragged last CTA
+        ns = 301                                   # > 2 CTAs of 128, ragged last CTA, odd
         pieces = [700, 64, 33, 1300]               # continuation across fills, ragged tails
         total = sum(pieces)
         ref = oracle.fill(gen, 77, ns, total, luxury=lux)
@@ -70,3 +70,21 @@ def test_tile_parity_jump(gen, tile):
         np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.serial_fill(gen, x0, n))
     finally:
         P.prng_set_tile(gen, 0, *saved)
+
+
+@pytest.mark.parametrize("tile", tune.TILES["mt19937"])
+def test_tile_parity_mt_jump(tile):
+    # 37 chunk rows (odd: with two streams per warp the last warp has an
+    # idle half) and a last row cut short by the element limit.
+    saved = P.prng_get_tile("mt19937")
+    P.prng_set_tile("mt19937", 0, *tile)
+    try:
+        n = 100003
+        out = torch.full((n + 4,), -7, dtype=torch.int32, device="cuda")
+        P.prng_fill_jump_u32("mt19937", 5489, n, 37, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(got[:n], oracle.serial_fill("mt19937", 5489, n))
+        assert np.all(got[n:] == np.uint32(2**32 - 7)), "write past the end"
+    finally:
+        P.prng_set_tile("mt19937", 0, *saved)
