@@ -38,47 +38,56 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
 
 // One twist of a stream's table (Appendix A, "Mersenne twister"), in place,
 // by the LPS lanes that own the stream (32: a warp; 16: half a warp, the
-// warp's other half twisting another stream in step), in chunks of 4 LPS
-// entries (five of 128 or ten of 64); lane u owns entries k .. k+3,
-// k = k0 + 4 u, read and written with 16-byte shared accesses.  Any chunk
-// size up to 227 keeps the in-place order valid.  The lag X_{k+397} is old
+// warp's other half twisting another stream in step), in chunks of
+// 4 LPS QPL entries (five of 128 for both forms); lane u owns the QPL quads
+// k .. k+3, k = k0 + 4 LPS q + 4 u, read and written with 16-byte shared
+// accesses, so each lane has QPL independent quads between two syncs.  Any
+// chunk size up to 227 keeps the in-place order valid.  The lag X_{k+397} is old
 // for k < 227 and already replaced (X_{k-227}) from 227 on; both start one
 // word past a 16-byte boundary, so they come from two aligned 16-byte loads.
 // Only the lane holding k = 224..227 straddles the switch.  Each new word is
 // tempered and, if o != null, written to o[k] (16-byte stores when VEC);
 // PARTIAL: only entries k < take are written.
-template <int OM, bool PARTIAL, int LPS = 32>
+template <int OM, bool PARTIAL, int LPS = 32, int QPL = 1>
 __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec,
                                          const FillDesc* d = nullptr, uint64_t e0 = 0) {
-  constexpr int CH = 4 * LPS;
+  constexpr int CH = 4 * LPS * QPL;
   static_assert(CH <= 227, "a chunk may not reach its own lags");
 #pragma unroll
   for (int k0 = 0; k0 < 624; k0 += CH) {
-    const int k = k0 + 4 * lane;
-    const bool valid = k < 624;
-    uint4 a = make_uint4(0, 0, 0, 0), f = a;
-    uint32_t b = 0;
-    if (valid) {
-      a = *reinterpret_cast<const uint4*>(s + k);
-      b = s[k + 4 == 624 ? 0 : k + 4];
-      const bool old_lag = (k0 + CH <= 227) || (k0 < 227 && k + 3 < 227);
-      const bool new_lag = (k0 >= 227) || k >= 227;
-      if (old_lag || new_lag) {
-        const int base = old_lag ? k + 396 : k - 228;
-        const uint4 q1 = *reinterpret_cast<const uint4*>(s + base);
-        const uint32_t q2 = s[base + 4];
-        f = make_uint4(q1.y, q1.z, q1.w, q2);
-      } else {  // k = 224: lags 621, 622, 623 (old) and 0 (new)
-        f = make_uint4(s[621], s[622], s[623], s[0]);
+    uint4 a[QPL], f[QPL];
+    uint32_t b[QPL];
+#pragma unroll
+    for (int q = 0; q < QPL; q++) {
+      const int k = k0 + 4 * LPS * q + 4 * lane;
+      a[q] = make_uint4(0, 0, 0, 0);
+      f[q] = a[q];
+      b[q] = 0;
+      if (k < 624) {
+        a[q] = *reinterpret_cast<const uint4*>(s + k);
+        b[q] = s[k + 4 == 624 ? 0 : k + 4];
+        const bool old_lag = (k0 + CH <= 227) || (k0 < 227 && k + 3 < 227);
+        const bool new_lag = (k0 >= 227) || k >= 227;
+        if (old_lag || new_lag) {
+          const int base = old_lag ? k + 396 : k - 228;
+          const uint4 q1 = *reinterpret_cast<const uint4*>(s + base);
+          const uint32_t q2 = s[base + 4];
+          f[q] = make_uint4(q1.y, q1.z, q1.w, q2);
+        } else {  // k = 224: lags 621, 622, 623 (old) and 0 (new)
+          f[q] = make_uint4(s[621], s[622], s[623], s[0]);
+        }
       }
     }
     __syncwarp();
-    if (valid) {
+#pragma unroll
+    for (int q = 0; q < QPL; q++) {
+      const int k = k0 + 4 * LPS * q + 4 * lane;
+      if (k >= 624) continue;
       uint4 v;
-      v.x = mt_mix(a.x, a.y, f.x);
-      v.y = mt_mix(a.y, a.z, f.y);
-      v.z = mt_mix(a.z, a.w, f.z);
-      v.w = mt_mix(a.w, b, f.w);
+      v.x = mt_mix(a[q].x, a[q].y, f[q].x);
+      v.y = mt_mix(a[q].y, a[q].z, f[q].y);
+      v.z = mt_mix(a[q].z, a[q].w, f[q].z);
+      v.w = mt_mix(a[q].w, b[q], f[q].w);
       *reinterpret_cast<uint4*>(s + k) = v;
       if (o != nullptr) {
         uint4 t;
@@ -120,7 +129,7 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
 // whole warp (a 624-word block is twisted as partial or unaligned if either
 // stream needs it), and a half whose row is past the end (inactive) runs
 // along without touching memory outside shared memory.
-template <int OM, int LPS = 32>
+template <int OM, int LPS = 32, int QPL = 1>
 __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane,
                                           bool active = true) {
   uint32_t* gs = d.state + row * 624;
@@ -156,16 +165,16 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
     bool whole = !store || j + 624 <= nv;
     if (LPS < 32) whole = __all_sync(0xFFFFFFFFu, whole);
     if (whole)
-      mt_twist<OM, false, LPS>(s, lane, store ? orow + j : nullptr, 624, vec, &d, row * d.pitch + j);
+      mt_twist<OM, false, LPS, QPL>(s, lane, store ? orow + j : nullptr, 624, vec, &d, row * d.pitch + j);
     else
-      mt_twist<OM, true, LPS>(s, lane, store ? orow + j : nullptr,
+      mt_twist<OM, true, LPS, QPL>(s, lane, store ? orow + j : nullptr,
                               (int)(store && nv > j ? (nv - j < 624 ? nv - j : 624) : 0), false, &d,
                               row * d.pitch + j);
     j += 624;
   }
   if (j < n) {
     const uint64_t take = store && nv > j ? (nv - j < n - j ? nv - j : n - j) : 0;
-    mt_twist<OM, true, LPS>(s, lane, store ? orow + j : nullptr, (int)take, false, &d, row * d.pitch + j);
+    mt_twist<OM, true, LPS, QPL>(s, lane, store ? orow + j : nullptr, (int)take, false, &d, row * d.pitch + j);
   }
   if (active)
     for (int k = lane; k < 624; k += LPS) gs[k] = s[k];
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(WPB * 32) k_fill_mt(const FillDesc d) {
   const uint64_t row0 = ((uint64_t)blockIdx.x * WPB + wi) * SPW;
   if (row0 >= d.n_rows) return;  // whole warp leaves; no CTA-wide barriers below
   const uint64_t row = row0 + half;
-  mt_stream<OM, LPS>(d, row, table[wi * SPW + half], lane % LPS, row < d.n_rows);
+  mt_stream<OM, LPS, SPW>(d, row, table[wi * SPW + half], lane % LPS, row < d.n_rows);
 }
 
 // Batched MT19937 fills: each warp pops an item (up to 2 streams of one
