@@ -719,12 +719,40 @@ def measure_batched(P, dev, args):
         pt.append(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host)))
         if done:
             lat = sorted(e0.elapsed_time(e) for e in done)
+    # The same two forms without the re-seed: fills only (every pass
+    # continues the streams, so the bytes differ between passes; the work
+    # does not).
+    fr_ns = [dict(r, reseed=False) for r in fr]
+    b_ns = P.prng_batch_create(fr_ns)
+    for _ in range(2):
+        P.prng_batch_launch(b_ns, sid)
+    torch.cuda.synchronize()
+    bt_ns = []
+    for _ in range(args.batch_passes):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        P.prng_batch_launch(b_ns, sid)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bt_ns.append(e0.elapsed_time(e1))
+    P.prng_batch_destroy(b_ns)
+    pt_ns = []
+    for _ in range(args.batch_passes):
+        t_host = time.perf_counter()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for h, q, o in zip(handles, reqs, offs):
+            (P.prng_fill_f32 if q["f32"] else P.prng_fill_u32)(h, base + 4 * o, q["n_per"], sid)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pt_ns.append(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host)))
     P.prng_batch_destroy(b)
     for h in handles:
         P.prng_destroy(h)
     del buf
     torch.cuda.empty_cache()
     bms, pms = statistics.median(bt), statistics.median(pt)
+    bns, pns = statistics.median(bt_ns), statistics.median(pt_ns)
     pct = lambda xs, q: xs[min(len(xs) - 1, int(q * len(xs)))]
     return {"requests": len(reqs), "numbers_per_pass": numbers, "work_items": info["items"],
             "batched": {"ms_per_pass": bms, "numbers_per_s": numbers / (bms / 1e3),
@@ -734,8 +762,15 @@ def measure_batched(P, dev, args):
                             "p99_ms": pct(lat, 0.99) if lat else None,
                             "launches_per_pass": 2 * len(reqs)},
             "speedup": pms / bms,
+            "without_seeding": {
+                "batched": {"ms_per_pass": bns, "numbers_per_s": numbers / (bns / 1e3),
+                            "launches_per_pass": 1},
+                "per_request": {"ms_per_pass": pns, "numbers_per_s": numbers / (pns / 1e3),
+                                "launches_per_pass": len(reqs)},
+                "speedup": pns / bns},
             "note": "per-request time is the larger of the device span and the host "
-                    "enqueue time of its launches"}
+                    "enqueue time of its launches; the main figures re-seed every request "
+                    "inside the pass, without_seeding times the fills alone"}
 
 
 def measure_serving(args):
