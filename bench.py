@@ -304,6 +304,12 @@ def rank_seed_base(g: str, rank: int) -> int:
     return SEED + rank * shape(g)[0]
 
 
+def rank_jump_first(rank: int) -> int:
+    """Rank `rank`'s jump fills cover draws [rank N, (rank + 1) N) of the one
+    sequence from x0 (N = JUMP_N), so that the ranks tile it."""
+    return rank * JUMP_N
+
+
 def max_over_ranks(value: float, dist, device) -> float:
     """The slowest rank's time (all-reduce MAX; a CUDA tensor under NCCL)."""
     import torch
@@ -522,7 +528,8 @@ def run_ours(args, rank, world, local_rank):
             elif kind == "f32":
                 P.prng_fill_f32(handles[g], out_f.data_ptr(), shape(g)[1], sid)
             else:
-                P.prng_fill_jump_u32(g, JUMP_X0[g], JUMP_N, JUMP_CHUNKS, out_u.data_ptr(), sid)
+                P.prng_fill_jump_at_u32(g, JUMP_X0[g], rank_jump_first(rank), JUMP_N, JUMP_CHUNKS,
+                                        out_u.data_ptr(), sid)
             if record:
                 e1.record(stream)
                 ev[lab].append((e0, e1))
@@ -609,7 +616,7 @@ def run_ours(args, rank, world, local_rank):
     # every output to pinned host memory inside the timed region.
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(P, handles, seed_r, items, dev, args)
+        e2e = measure_e2e(P, handles, seed_r, items, dev, args, rank)
 
     for h in handles.values():
         P.prng_destroy(h)
@@ -804,7 +811,7 @@ def measure_serving(args):
     return out
 
 
-def measure_e2e(P, handles, seed_r, items, dev, args):
+def measure_e2e(P, handles, seed_r, items, dev, args, rank=0):
     """The step end to end through the C ABI with host outputs: every fill
     writes its numbers into page-locked host memory from prng_host_alloc, so
     the kernels' stores cross the host link (NVLink-C2C) and no device
@@ -827,8 +834,8 @@ def measure_e2e(P, handles, seed_r, items, dev, args):
             elif kind == "f32":
                 P.prng_fill_f32(handles[g], host.ptr, shape(g)[1], stream.cuda_stream)
             else:
-                P.prng_fill_jump_u32(g, JUMP_X0[g], JUMP_N, JUMP_CHUNKS, host.ptr,
-                                     stream.cuda_stream)
+                P.prng_fill_jump_at_u32(g, JUMP_X0[g], rank_jump_first(rank), JUMP_N, JUMP_CHUNKS,
+                                        host.ptr, stream.cuda_stream)
             d2h += 4 * numbers
 
     try:

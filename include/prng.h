@@ -156,6 +156,19 @@ int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunk
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        float *d_out, void *stream);
 
+/* The same single-sequence fill from position `first` on: draws first+1 ..
+ * first+n of the sequence started at x0 go to d_out[0..n), so that disjoint
+ * ranges (one per GPU, say) tile one long sequence.  The start is moved
+ * `first` draws on once (GGL, RANECU: a^first by square-and-multiply on the
+ * host; XOR128: T^first over GF(2); MT19937: one application of the jump
+ * polynomial of `first`), then chunked as above.  PRNG_ESIZE if first + n
+ * overflows 64 bits; otherwise as prng_fill_jump_*; first = 0 is exactly
+ * prng_fill_jump_*. */
+int prng_fill_jump_at_u32(prng_gen_t gen, uint64_t x0, uint64_t first, uint64_t n,
+                          uint32_t n_chunks, uint32_t *d_out, void *stream);
+int prng_fill_jump_at_f32(prng_gen_t gen, uint64_t x0, uint64_t first, uint64_t n,
+                          uint32_t n_chunks, float *d_out, void *stream);
+
 /* ---------------------------------------------------------------- batches
  * Many fills on distinct handles run as one pass: the plan cuts every
  * request into work items (a range of its streams), orders each generator

@@ -80,6 +80,8 @@ def lib():
             L.orc_mt_charpoly_info.argtypes = [ctypes.POINTER(i32)]
             L.orc_mt_next.restype = u32
             L.orc_mt_next.argtypes = [vp]
+            L.orc_xor128_next.restype = u32
+            L.orc_xor128_next.argtypes = [vp]
             L.orc_serial_sample.restype = ctypes.c_int
             L.orc_serial_sample.argtypes = [i32, u64, vp, u64, vp]
             L.orc_serial_fill.restype = ctypes.c_int
@@ -199,6 +201,17 @@ def xor128_jump(state, k: int):
     s = np.ascontiguousarray(np.asarray(state, dtype=np.uint32).copy())
     lib().orc_xor128_jump(s.ctypes.data, k & (2**64 - 1))
     return s
+
+
+def xor128_draws_from(state, n: int):
+    """n outputs of XOR128 from an explicit state (x, y, z, w)."""
+    class _X(ctypes.Structure):
+        _fields_ = [("x", ctypes.c_uint32), ("y", ctypes.c_uint32), ("z", ctypes.c_uint32),
+                    ("w", ctypes.c_uint32)]
+    x, y, z, w = (int(v) for v in state)
+    s = _X(x, y, z, w)
+    L = lib()
+    return np.array([L.orc_xor128_next(ctypes.byref(s)) for _ in range(n)], dtype=np.uint32)
 
 
 def mt_jump(table, mti: int, k: int):

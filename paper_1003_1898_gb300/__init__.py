@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         "prng_set_state": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
         "prng_fill_jump_u32": ([ctypes.c_int, u64, u64, u32, vp, vp], ctypes.c_int),
         "prng_fill_jump_f32": ([ctypes.c_int, u64, u64, u32, vp, vp], ctypes.c_int),
+        "prng_fill_jump_at_u32": ([ctypes.c_int, u64, u64, u64, u32, vp, vp], ctypes.c_int),
+        "prng_fill_jump_at_f32": ([ctypes.c_int, u64, u64, u64, u32, vp, vp], ctypes.c_int),
         "prng_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u32),
                        ctypes.POINTER(u64)], ctypes.c_int),
         "prng_set_tile": ([ctypes.c_int, u32, u32, u32, u32], ctypes.c_int),
@@ -175,6 +177,16 @@ def prng_fill_jump_u32(gen, x0: int, n: int, n_chunks: int, out, stream=None):
 def prng_fill_jump_f32(gen, x0: int, n: int, n_chunks: int, out, stream=None):
     _check(lib().prng_fill_jump_f32(_gen(gen), x0, n, n_chunks, _ptr(out), _stream(stream)),
            "prng_fill_jump_f32")
+
+
+def prng_fill_jump_at_u32(gen, x0: int, first: int, n: int, n_chunks: int, out, stream=None):
+    _check(lib().prng_fill_jump_at_u32(_gen(gen), x0, first, n, n_chunks, _ptr(out), _stream(stream)),
+           "prng_fill_jump_at_u32")
+
+
+def prng_fill_jump_at_f32(gen, x0: int, first: int, n: int, n_chunks: int, out, stream=None):
+    _check(lib().prng_fill_jump_at_f32(_gen(gen), x0, first, n, n_chunks, _ptr(out), _stream(stream)),
+           "prng_fill_jump_at_f32")
 
 
 def prng_info(h) -> dict:

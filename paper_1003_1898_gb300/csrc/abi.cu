@@ -62,18 +62,29 @@ int fill_impl(prng_state* st, void* d_out, uint64_t n_per, int mode, cudaStream_
   return PRNG_OK;
 }
 
-int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
-              cudaStream_t s) {
+// a^e mod m on the host, for a, m < 2^31 (products stay below 2^62).
+uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t m) {
+  uint64_t r = 1, b = a % m;
+  for (; e; e >>= 1) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+  }
+  return r;
+}
+
+int jump_impl(int gen, uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks, void* d_out,
+              int f32, cudaStream_t s) {
   if (gen < 0 || gen > 5) return PRNG_EGEN;
   if (gen != GGL && gen != RANECU && gen != XOR128 && gen != MT19937) return PRNG_EUNSUPPORTED;
   if (n == 0) return PRNG_OK;
   if (d_out == nullptr) return PRNG_ENULL;
   if (n_chunks == 0) return PRNG_ESIZE;
+  if (n > ~0ull - first) return PRNG_ESIZE;
   if ((reinterpret_cast<uintptr_t>(d_out) & 3) != 0) return PRNG_ESIZE;
   if (gen == XOR128 || gen == MT19937) {
     if (gen == MT19937 && x0 > 0xFFFFFFFFull) return PRNG_ESEED;
-    const cudaError_t e = gen == XOR128 ? launch_jump_xor128(x0, n, n_chunks, d_out, f32, s)
-                                        : launch_jump_mt(x0, n, n_chunks, d_out,
+    const cudaError_t e = gen == XOR128 ? launch_jump_xor128(x0, first, n, n_chunks, d_out, f32, s)
+                                        : launch_jump_mt(x0, first, n, n_chunks, d_out,
                                                          f32 ? OUT_F32 : OUT_U32, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -81,11 +92,16 @@ int jump_impl(int gen, uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, 
     }
     return PRNG_OK;
   }
+  // The start moved `first` draws on: x_first = a^first x0 (per component).
   if (gen == GGL) {
     if (x0 == 0 || x0 >= 2147483647ull) return PRNG_ESEED;
+    x0 = host_powmod(16807, first, 2147483647ull) * x0 % 2147483647ull;
   } else {
-    const uint64_t s1 = x0 & 0xFFFFFFFFull, s2 = x0 >> 32;
+    uint64_t s1 = x0 & 0xFFFFFFFFull, s2 = x0 >> 32;
     if (s1 == 0 || s1 >= 2147483563ull || s2 == 0 || s2 >= 2147483399ull) return PRNG_ESEED;
+    s1 = host_powmod(40014, first, 2147483563ull) * s1 % 2147483563ull;
+    s2 = host_powmod(40692, first, 2147483399ull) * s2 % 2147483399ull;
+    x0 = s1 | (s2 << 32);
   }
   // The generator's fill tile decides the kernel.  The lane-parallel one
   // runs a warp per chunk as asked; the staged one runs a thread per chunk,
@@ -370,12 +386,22 @@ int prng_set_state(prng_state* st, const void* h_buf, size_t bytes) {
 
 int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        uint32_t* d_out, void* stream) {
-  return jump_impl((int)gen, x0, n, n_chunks, d_out, 0, static_cast<cudaStream_t>(stream));
+  return jump_impl((int)gen, x0, 0, n, n_chunks, d_out, 0, static_cast<cudaStream_t>(stream));
 }
 
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        float* d_out, void* stream) {
-  return jump_impl((int)gen, x0, n, n_chunks, d_out, 1, static_cast<cudaStream_t>(stream));
+  return jump_impl((int)gen, x0, 0, n, n_chunks, d_out, 1, static_cast<cudaStream_t>(stream));
+}
+
+int prng_fill_jump_at_u32(prng_gen_t gen, uint64_t x0, uint64_t first, uint64_t n,
+                          uint32_t n_chunks, uint32_t* d_out, void* stream) {
+  return jump_impl((int)gen, x0, first, n, n_chunks, d_out, 0, static_cast<cudaStream_t>(stream));
+}
+
+int prng_fill_jump_at_f32(prng_gen_t gen, uint64_t x0, uint64_t first, uint64_t n,
+                          uint32_t n_chunks, float* d_out, void* stream) {
+  return jump_impl((int)gen, x0, first, n, n_chunks, d_out, 1, static_cast<cudaStream_t>(stream));
 }
 
 int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t cols,

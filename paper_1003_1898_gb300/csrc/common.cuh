@@ -113,14 +113,14 @@ struct MtPoly {
 cudaError_t launch_mt_poly_apply(const MtPoly& g, uint32_t* state, uint64_t r0, uint64_t r1,
                                  uint64_t src_off, cudaStream_t s);
 cudaError_t launch_skip_mt(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s);
-cudaError_t launch_jump_mt(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int mode,
-                           cudaStream_t s);
+cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks,
+                           void* d_out, int mode, cudaStream_t s);
 
 // XOR128 jump-ahead over GF(2): prng_skip of k steps on a handle's state
 // (struct-of-arrays [4][n]), and the single-sequence chunked fill.
 cudaError_t launch_skip_xor128(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t s);
-cudaError_t launch_jump_xor128(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
-                               cudaStream_t s);
+cudaError_t launch_jump_xor128(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks,
+                               void* d_out, int f32, cudaStream_t s);
 
 // ------------------------------------------------------------------ device
 

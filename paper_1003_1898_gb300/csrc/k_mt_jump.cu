@@ -208,8 +208,8 @@ cudaError_t launch_skip_mt(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t
   return launch_mt_poly_apply(jump_poly(k), state, 0, n, 0, s);
 }
 
-cudaError_t launch_jump_mt(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int mode,
-                           cudaStream_t s) {
+cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks,
+                           void* d_out, int mode, cudaStream_t s) {
   const uint64_t L = (n + n_chunks - 1) / n_chunks;   // draws per chunk
   const uint64_t C = (n + L - 1) / L;                 // chunks, none empty
   HostMt mt;
@@ -218,6 +218,8 @@ cudaError_t launch_jump_mt(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_o
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S), C * 624 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(S, mt.mt, sizeof(mt.mt), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && first > 0)   // the start table moved `first` words on, in place
+    e = launch_mt_poly_apply(jump_poly(first), S, 0, 1, 0, s);
   // Pass i: chunks [2^i, 2^(i+1)) from chunks [0, 2^i), L 2^i outputs on.
   int i = 0;
   for (uint64_t half = 1; e == cudaSuccess && half < C; half <<= 1, i++)

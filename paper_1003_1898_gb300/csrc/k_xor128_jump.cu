@@ -159,8 +159,8 @@ cudaError_t launch_skip_xor128(uint32_t* state, uint64_t n, uint64_t k, cudaStre
   return apply_rows(M, state, n, 0, n, 0, s);
 }
 
-cudaError_t launch_jump_xor128(uint64_t x0, uint64_t n, uint32_t n_chunks, void* d_out, int f32,
-                               cudaStream_t s) {
+cudaError_t launch_jump_xor128(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks,
+                               void* d_out, int f32, cudaStream_t s) {
   // The fill kernel runs one thread per chunk, so the chunks are cut finer
   // when there are too few to fill the GPU (any contiguous cut of the one
   // sequence gives the same output), down to 64 draws per chunk.
@@ -177,6 +177,7 @@ cudaError_t launch_jump_xor128(uint64_t x0, uint64_t n, uint32_t n_chunks, void*
   if (e != cudaSuccess) return e;
   k_xor128_set_row<<<1, 1, 0, s>>>(S, C, 0, v0[0], v0[1], v0[2], v0[3]);
   e = cudaGetLastError();
+  if (e == cudaSuccess && first > 0) e = apply_rows(step_power(first), S, C, 0, 1, 0, s);  // to `first`
   // Pass i: chunks [2^i, 2^(i+1)) from chunks [0, 2^i) by T^(L 2^i).
   int i = 0;
   for (uint64_t half = 1; e == cudaSuccess && half < C; half <<= 1, i++)

@@ -62,6 +62,12 @@ def test_jump_rejects_bad_arguments(L):
     assert L.prng_fill_jump_u32(P.GGL, 1, 10, 0, buf, None) == -3
     assert L.prng_fill_jump_u32(P.GGL, 1, 10, 1, None, None) == -4
     assert L.prng_fill_jump_u32(P.GGL, 1, 0, 1, None, None) == 0          # empty: no-op
+    assert L.prng_fill_jump_at_u32(P.GGL, 1, 2**64 - 5, 10, 1, buf, None) == -3   # first + n overflows
+    assert L.prng_fill_jump_at_u32(P.RANMAR, 1, 0, 10, 1, buf, None) == -7
+    assert L.prng_fill_jump_at_u32(P.MT19937, 2**32, 5, 10, 1, buf, None) == -9
+    assert L.prng_fill_jump_at_u32(P.GGL, 0, 5, 10, 1, buf, None) == -9
+    assert L.prng_fill_jump_at_f32(P.XOR128, 1, 5, 10, 1, None, None) == -4
+    assert L.prng_fill_jump_at_u32(P.GGL, 1, 5, 0, 1, None, None) == 0       # empty: no-op
 
 
 def test_null_handles(L):

@@ -297,6 +297,55 @@ def test_jump_fill_other_start(gen):
     np.testing.assert_array_equal(u32(out), oracle.serial_fill(gen, x0, n))
 
 
+def _jump_ref(gen, x0, first, n):
+    """Draws first+1 .. first+n of the single sequence from x0, by the
+    oracle: its start moved `first` draws on with the oracle's own jump
+    (GGL, XOR128, MT19937) or modular power (RANECU, per component), then
+    stepped serially."""
+    if gen == "ggl":
+        return oracle.serial_fill("ggl", oracle.ggl_jump(x0, first), n)
+    if gen == "ranecu":
+        s1 = oracle.modpow(40014, first, 2147483563) * (x0 & 0xFFFFFFFF) % 2147483563
+        s2 = oracle.modpow(40692, first, 2147483399) * (x0 >> 32) % 2147483399
+        return oracle.serial_fill("ranecu", s1 | (s2 << 32), n)
+    if gen == "xor128":
+        t = oracle.splitmix64(x0)
+        st = [x0 & 0xFFFFFFFF, (x0 >> 32) & 0xFFFFFFFF, t & 0xFFFFFFFF, t >> 32]
+        return oracle.xor128_draws_from(oracle.xor128_jump(st, first), n)
+    return oracle.mt_draws_from(oracle.mt_jump(oracle.mt_init_table(x0), 624, first), 624, n)
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
+@pytest.mark.parametrize("first", [0, 1, 123457, 2**40 + 3, 2**63 + 5])
+def test_jump_fill_at_offset(gen, first):
+    x0 = inputs.JUMP_X0[gen]
+    n, chunks = 20011, 37
+    out = torch.full((n + 4,), -7, dtype=torch.int32, device="cuda")
+    P.prng_fill_jump_at_u32(gen, x0, first, n, chunks, out.data_ptr())
+    torch.cuda.synchronize()
+    got = u32(out)
+    np.testing.assert_array_equal(got[:n], _jump_ref(gen, x0, first, n))
+    assert np.all(got[n:] == np.uint32(2**32 - 7)), "write past the end"
+    if first < 10**6:   # small offsets: the plain serial oracle directly
+        np.testing.assert_array_equal(got[:n], oracle.serial_sample(gen, x0, first + np.arange(n)))
+
+
+@pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
+def test_jump_fill_at_ranges_tile_one_sequence(gen):
+    # Two ranks' ranges [0, n) and [n, 2n), as f32, equal the one fill of 2n.
+    x0 = inputs.JUMP_X0[gen]
+    n = 30000
+    whole = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    P.prng_fill_jump_f32(gen, x0, 2 * n, 64, whole)
+    parts = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    P.prng_fill_jump_at_f32(gen, x0, 0, n, 32, parts[:n])
+    P.prng_fill_jump_at_f32(gen, x0, n, n, 32, parts[n:])
+    torch.cuda.synchronize()
+    assert torch.equal(whole.view(torch.int32), parts.view(torch.int32))
+    ref = oracle.to_f32(gen, oracle.serial_fill(gen, x0, 2 * n))
+    np.testing.assert_array_equal(parts.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
 # ------------------------------------------------------------ full sizes (sampled)
 
 def _sampled_rows_check(gen, lux, ns, nper, n_rows_checked, dtype="u32"):

@@ -1,7 +1,8 @@
 """The multi-GPU benchmark path's host logic on CPU, as two gloo ranks on
 127.0.0.1 (no GPU, no NCCL).  Per rank: its streams, seeded from
 bench.rank_seed_base, are streams [r n, (r + 1) n) of one handle of 2 n
-streams (checked with the oracle on sampled streams); the timing reduction
+streams (checked with the oracle on sampled streams); its jump fills cover
+the next N draws of the one sequence after the previous rank's; the timing reduction
 returns the slowest rank's time on every rank; the reference arm prints its
 JSON line from rank 0 only."""
 import argparse
@@ -45,6 +46,7 @@ def _worker(rank, world, port, q):
                 glob = oracle.sample(g, bench.SEED, rank * n + i, pos, luxury=lux)
                 checks.append(bool(np.array_equal(mine, glob)))
         out["partition_ok"] = all(checks)
+        out["jump_first"] = bench.rank_jump_first(rank)
         out["bases"] = {g: bench.rank_seed_base(g, rank) for g in bench.GENS}
         out["max_ms"] = bench.max_over_ranks(10.0 + rank, dist, "cpu")
         buf = io.StringIO()
@@ -81,6 +83,8 @@ def test_two_gloo_ranks_partition_reduce_and_print():
     import bench
     for g in bench.GENS:   # disjoint, adjacent stream ranges
         assert res[1]["bases"][g] - res[0]["bases"][g] == bench.shape(g)[0]
+    # jump fills: rank r covers draws [r N, (r + 1) N) of the one sequence
+    assert res[0]["jump_first"] == 0 and res[1]["jump_first"] == bench.JUMP_N
     assert res[1]["printed"] == ""
     lines = [l for l in res[0]["printed"].splitlines() if l.strip()]
     assert len(lines) == 1
