@@ -495,3 +495,15 @@ def test_ggl_output_range_and_ranmar_rmarin_ranges():
     for ij, kl in [(0, 0), (31328, 30081), (1802, 9373)]:
         r = oracle.explicit_draws("ranmar", [ij, kl], 100)
         assert r.max() < 2**24
+
+
+def test_xor128_draws_from_state_continue_the_serial_sequence():
+    # From the seeding-map start state the helper gives the serial sequence,
+    # and from the state jumped k on (GF(2) matrix power) its continuation.
+    x0 = 0x5EED
+    t = oracle.splitmix64(x0)
+    st = [x0 & 0xFFFFFFFF, x0 >> 32, t & 0xFFFFFFFF, t >> 32]
+    ref = oracle.serial_fill("xor128", x0, 3000)
+    np.testing.assert_array_equal(oracle.xor128_draws_from(st, 3000), ref)
+    np.testing.assert_array_equal(oracle.xor128_draws_from(oracle.xor128_jump(st, 1234), 1766),
+                                  ref[1234:])
