@@ -38,6 +38,30 @@ class PrngFillReq(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("f32", ctypes.c_uint32), ("reseed", ctypes.c_uint32)]
 
 
+def _np_dtype(struct):
+    """numpy structured dtype with the exact field offsets and size of a
+    ctypes struct, so arrays of it can be handed to the library as is."""
+    import numpy as np
+    fmt = {ctypes.c_void_p: "<u8", ctypes.c_uint64: "<u8", ctypes.c_uint32: "<u4"}
+    names = [n for n, _ in struct._fields_]
+    return np.dtype({"names": names, "formats": [fmt[t] for _, t in struct._fields_],
+                     "offsets": [getattr(struct, n).offset for n in names],
+                     "itemsize": ctypes.sizeof(struct)})
+
+
+FILL_REQ_DTYPE = _np_dtype(PrngFillReq)
+ISING_REQ_DTYPE = _np_dtype(PrngIsingReq)
+
+
+def _struct_rows(rows, dtype, struct):
+    """(pointer, count) of a numpy array of `dtype` rows, passed as is."""
+    import numpy as np
+    arr = np.ascontiguousarray(rows)
+    if arr.dtype != dtype:
+        raise TypeError(f"expected rows of {dtype}")
+    return arr, arr.ctypes.data_as(ctypes.POINTER(struct)), arr.shape[0]
+
+
 class PrngError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {prng_strerror(code)} (code {code})")
@@ -262,7 +286,12 @@ def prng_batcher_create(max_requests: int, max_items: int) -> ctypes.c_void_p:
 
 
 def prng_batcher_launch(b, reqs, stream=None):
-    arr, n = _fill_req_array(reqs)
+    """reqs: dicts as for prng_batch_create, or a numpy array of
+    FILL_REQ_DTYPE rows (passed to the library without conversion)."""
+    if hasattr(reqs, "dtype"):
+        keep, arr, n = _struct_rows(reqs, FILL_REQ_DTYPE, PrngFillReq)
+    else:
+        arr, n = _fill_req_array(reqs)
     _check(lib().prng_batcher_launch(b, arr, n, _stream(stream)), "prng_batcher_launch")
 
 
@@ -284,7 +313,12 @@ def prng_ising_half_sweep(reqs, stream=None):
     """reqs: iterable of dicts with d_spins, d_draws, L, colour, gen (or
     shift), t4, t8, and optionally per and pitch (the draws of the
     half-sweep as per-word columns of rows `pitch` words apart); d_draws may
-    be an integer device address."""
+    be an integer device address.  A numpy array of ISING_REQ_DTYPE rows is
+    passed to the library without conversion."""
+    if hasattr(reqs, "dtype"):
+        keep, arr, n = _struct_rows(reqs, ISING_REQ_DTYPE, PrngIsingReq)
+        _check(lib().prng_ising_half_sweep(arr, n, _stream(stream)), "prng_ising_half_sweep")
+        return
     reqs = list(reqs)
     arr = (PrngIsingReq * max(1, len(reqs)))()
     for i, r in enumerate(reqs):

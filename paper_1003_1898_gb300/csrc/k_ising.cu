@@ -13,6 +13,12 @@
 //
 // Up to kIsingPerLaunch lattices go to one launch with their descriptors
 // passed by value; a block works on one lattice (block ranges by prefix).
+// Lattices whose rows split into 16-byte chunks (L a multiple of 16, both
+// buffers 16-byte aligned, and a draw layout that keeps 8 consecutive
+// ranks in one row) take the vector form: a thread owns 16 consecutive
+// sites of a row, 8 of them of the colour, and moves them as one 16-byte
+// load and store per row (its own row and the rows above and below) and two
+// 16-byte draw loads.  The others take the scalar form, a thread per site.
 #include <cmath>
 
 #include "../../include/prng.h"
@@ -66,6 +72,74 @@ __global__ void __launch_bounds__(kIsingThreads) k_ising_half_sweep(const __grid
   }
 }
 
+// Vector form.  The 16-byte store also rewrites the 8 sites of the other
+// colour with the values it read: nothing changes them during the
+// half-sweep, so readers of those neighbours see the same bytes.
+constexpr int kIsingVecThreads = 256;
+
+__device__ __forceinline__ uint32_t ising_lattice_of(const IsingLaunch& b) {
+  uint32_t lo = 0, hi = b.n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (b.block0[mid] <= blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kIsingVecThreads) k_ising_half_sweep_v(const __grid_constant__ IsingLaunch b) {
+  const uint32_t lo = ising_lattice_of(b);
+  const prng_ising_req& q = b.r[lo];
+  const uint32_t L = q.L, cpr = L >> 4;                      // 16-site chunks per row
+  const uint32_t chunk = (blockIdx.x - b.block0[lo]) * kIsingVecThreads + threadIdx.x;
+  if (chunk >= L * cpr) return;                              // L <= 65534: L * L / 16 < 2^28
+  const uint32_t y = chunk / cpr, x0 = (chunk - y * cpr) << 4;
+  const uint32_t yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+  int8_t* row = q.d_spins + (uint64_t)y * L;
+  union V { uint4 v; int8_t c[16]; };
+  V C, U, D;
+  C.v = *reinterpret_cast<const uint4*>(row + x0);
+  U.v = *reinterpret_cast<const uint4*>(q.d_spins + (uint64_t)yu * L + x0);
+  D.v = *reinterpret_cast<const uint4*>(q.d_spins + (uint64_t)yd * L + x0);
+  const int lft = row[x0 == 0 ? L - 1 : x0 - 1];
+  const int rgt = row[x0 + 16 == L ? 0 : x0 + 16];
+  const uint32_t par = (y + q.colour) & 1u;                 // x parity of the colour in row y
+  const uint32_t k0 = y * (L >> 1) + (x0 >> 1);              // colour rank of the first site
+  uint64_t di = k0;
+  if (q.pitch != 0) {   // 8 ranks never straddle a row of `per` (per % 8 == 0)
+    const uint32_t per = q.per;
+    const uint32_t pr = (per & (per - 1)) == 0 ? k0 >> (__ffs(per) - 1) : k0 / per;
+    di = (uint64_t)pr * q.pitch + (k0 - pr * per);
+  }
+  const uint4 d0 = *reinterpret_cast<const uint4*>(q.d_draws + di);
+  const uint4 d1 = *reinterpret_cast<const uint4*>(q.d_draws + di + 4);
+  const uint32_t dr[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+  V O = C;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+#pragma unroll
+    for (int p = 0; p < 2; p++) {     // compile-time byte index for each parity
+      if ((uint32_t)p != par) continue;
+      const int bi = 2 * i + p;
+      const int s = C.c[bi];
+      const int l = bi == 0 ? lft : C.c[bi - 1];
+      const int r = bi == 15 ? rgt : C.c[bi + 1];
+      const int dE = 2 * s * (U.c[bi] + D.c[bi] + l + r);
+      const uint32_t v = dr[i] >> q.shift;
+      const bool accept = dE <= 0 || (dE == 4 ? v < q.t4 : v < q.t8);
+      if (accept) O.c[bi] = (int8_t)(-s);
+    }
+  }
+  *reinterpret_cast<uint4*>(row + x0) = O.v;
+}
+
+// Whether a lattice can take the vector form.
+static bool ising_vec_ok(const prng_ising_req& q) {
+  return (q.L & 15u) == 0 && q.L <= 65520 && (reinterpret_cast<uintptr_t>(q.d_spins) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(q.d_draws) & 15) == 0 &&
+         (q.pitch == 0 || ((q.per & 7u) == 0 && (q.pitch & 3u) == 0));
+}
+
 }  // namespace prng
 
 using namespace prng;
@@ -81,21 +155,32 @@ extern "C" int prng_ising_half_sweep(const prng_ising_req* reqs, uint32_t n, voi
     if ((reinterpret_cast<uintptr_t>(q.d_draws) & 3) != 0) return PRNG_ESIZE;
   }
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  constexpr uint64_t per_block = (uint64_t)kIsingThreads * kIsingSitesPerThread;
-  for (uint32_t first = 0; first < n; first += kIsingPerLaunch) {
+  // Each group of up to kIsingPerLaunch lattices: the vector-form ones in one
+  // launch, the rest in another (a thread per 16 sites / per 4 sites).
+  for (int vec = 1; vec >= 0; vec--) {
+    const uint64_t per_block = vec ? (uint64_t)kIsingVecThreads * 16
+                                   : (uint64_t)kIsingThreads * kIsingSitesPerThread * 2;
     IsingLaunch b;
-    b.n = n - first < (uint32_t)kIsingPerLaunch ? n - first : (uint32_t)kIsingPerLaunch;
+    b.n = 0;
     uint64_t blocks = 0;
-    for (uint32_t i = 0; i < b.n; i++) {
-      b.r[i] = reqs[first + i];
-      b.block0[i] = (uint32_t)blocks;
-      const uint64_t sites = (uint64_t)b.r[i].L * (b.r[i].L / 2);
-      blocks += (sites + per_block - 1) / per_block;
+    auto flush = [&]() -> bool {
+      if (b.n == 0) return true;
+      if (blocks > 0x7FFFFFFFull) return false;
+      b.block0[b.n] = (uint32_t)blocks;
+      if (vec) k_ising_half_sweep_v<<<(unsigned)blocks, kIsingVecThreads, 0, s>>>(b);
+      else k_ising_half_sweep<<<(unsigned)blocks, kIsingThreads, 0, s>>>(b);
+      b.n = 0;
+      blocks = 0;
+      return cudaGetLastError() == cudaSuccess;
+    };
+    for (uint32_t i = 0; i < n; i++) {
+      if (ising_vec_ok(reqs[i]) != (vec == 1)) continue;
+      b.r[b.n] = reqs[i];
+      b.block0[b.n] = (uint32_t)blocks;
+      blocks += ((uint64_t)reqs[i].L * reqs[i].L + per_block - 1) / per_block;   // L * L sites
+      if (++b.n == (uint32_t)kIsingPerLaunch && !flush()) return blocks > 0x7FFFFFFFull ? PRNG_ESIZE : PRNG_ECUDA;
     }
-    if (blocks > 0x7FFFFFFFull) return PRNG_ESIZE;
-    b.block0[b.n] = (uint32_t)blocks;
-    k_ising_half_sweep<<<(unsigned)blocks, kIsingThreads, 0, s>>>(b);
-    if (cudaGetLastError() != cudaSuccess) return PRNG_ECUDA;
+    if (!flush()) return blocks > 0x7FFFFFFFull ? PRNG_ESIZE : PRNG_ECUDA;
   }
   return PRNG_OK;
 }

@@ -27,8 +27,9 @@ import collections
 import dataclasses
 import time
 
-from . import (GEN_IDS, SHIFT, prng_batcher_create, prng_batcher_destroy, prng_batcher_launch,
-               prng_create, prng_destroy, prng_info, prng_ising_half_sweep, prng_ising_thresholds)
+from . import (FILL_REQ_DTYPE, GEN_IDS, ISING_REQ_DTYPE, SHIFT, prng_batcher_create,
+               prng_batcher_destroy, prng_batcher_launch, prng_create, prng_destroy, prng_info,
+               prng_ising_half_sweep, prng_ising_thresholds)
 
 ISING_BETA = 0.4406868
 
@@ -125,7 +126,15 @@ class Server:
         """Serve `requests` (sorted by arrival).  With realtime the loop
         releases each request at its arrival time; otherwise all are
         available at once.  Returns the requests with their completion
-        times."""
+        times.
+
+        Each request's launch rows (its fill descriptor, and for an Ising
+        run its half-sweep descriptors of either colour) are written once,
+        at admission, into numpy tables laid out as the library's structs;
+        a tick gathers the rows of the running requests with array
+        indexing, so its host cost does not grow with Python work per
+        request."""
+        import numpy as np
         torch = self.torch
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in reqs:
@@ -134,6 +143,12 @@ class Server:
                     raise ValueError("L*L/2 must be a multiple of the client's stream count")
             elif r.n <= 0:
                 raise ValueError("fill requests need n > 0")
+        n_req = len(reqs)
+        fill_tab = np.zeros(n_req, FILL_REQ_DTYPE)           # row of request i
+        ising_tab = np.zeros((n_req, 2), ISING_REQ_DTYPE)    # its half-sweeps, colour 0 / 1
+        per_tab = np.zeros(n_req, np.int64)                  # Ising draws per stream and half-sweep
+        half_done = np.zeros(n_req, np.int64)
+        half_total = np.zeros(n_req, np.int64)
         pending = collections.deque()
         inflight = collections.deque()         # (end event, [requests finishing])
         nxt = 0
@@ -141,8 +156,10 @@ class Server:
         with torch.cuda.stream(self.stream):
             t_start.record(self.stream)
         wall0 = time.perf_counter()
-        running = []                           # Ising requests in progress
-        left = len(reqs)
+        running = np.zeros(0, np.int64)        # Ising requests in progress (indices into reqs)
+        left = n_req
+        hpt = self.hpt
+        sid = self.stream.cuda_stream
 
         def retire(block: bool):
             nonlocal left
@@ -161,52 +178,28 @@ class Server:
 
         while left > 0:
             now = time.perf_counter() - wall0
-            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
-                pending.append(reqs[nxt])
+            while nxt < n_req and (not realtime or reqs[nxt].arrival <= now):
+                pending.append(nxt)
                 nxt += 1
             retire(False)
             if len(inflight) >= self.max_inflight:
                 retire(True)
                 continue
-            fills, steps, finishing = [], [], []
-            taken = set()
-
-            def ising_tick(r, c):
-                # The request's next h half-sweeps: one fill of h blocks per
-                # stream (row pitch h * per), then half-sweep t reads column
-                # block t of every row.
-                per = r.L * r.L // (2 * self.n_streams)
-                h = min(self.hpt, 2 * r.sweeps - r.half_done)
-                fills.append({"st": c.handle, "d_out": r.draws, "n_per_stream": h * per})
-                base = r.draws.data_ptr()
-                for t in range(h):
-                    while len(steps) <= t:
-                        steps.append([])
-                    steps[t].append({"d_spins": r.spins, "d_draws": base + 4 * t * per, "L": r.L,
-                                     "colour": (r.half_done + t) % 2, "shift": SHIFT[c.gen],
-                                     "t4": self.t4, "t8": self.t8, "per": per,
-                                     "pitch": h * per if h > 1 else 0})
-                r.half_done += h
-                r.numbers += h * (r.L * r.L // 2)
-                if r.half_done == 2 * r.sweeps:
-                    finishing.append(r)
-
-            for r in running:                  # next half-sweeps of each running Ising run
-                c = self.clients[r.client]
-                taken.add(r.client)
-                ising_tick(r, c)
+            new_fills, new_ising, finishing = [], [], []
+            taken = set()                      # clients admitted this tick (one request each)
             keep = collections.deque()
             active = len(running) + sum(len(f) for _, f in inflight)
             while pending:                      # admission in arrival order
-                r = pending.popleft()
+                i = pending.popleft()
+                r = reqs[i]
                 c = self.clients[r.client]
                 need = self.request_bytes(r)
                 if self.max_active and active >= self.max_active:
-                    keep.append(r)
+                    keep.append(i)
                     continue
                 active += 1
                 if r.client in taken or c.busy is not None or self.mem_used + need > self.mem_cap:
-                    keep.append(r)
+                    keep.append(i)
                     taken.add(r.client)         # a client's later requests wait behind this one
                     continue
                 taken.add(r.client)
@@ -216,22 +209,31 @@ class Server:
                         per, total = self.fill_shape(r.n)
                         r.out = torch.empty(total, dtype=torch.float32 if r.f32 else torch.int32,
                                             device="cuda")
-                        fills.append({"st": c.handle, "d_out": r.out, "n_per_stream": per,
-                                      "n_valid": r.n, "f32": r.f32})
+                        fill_tab[i] = (c.handle.value, r.out.data_ptr(), per, r.n, 0, int(r.f32), 0)
                         r.numbers = r.n
+                        new_fills.append(i)
                         finishing.append(r)
                     else:
+                        per = r.L * r.L // (2 * self.n_streams)
                         r.spins = torch.ones((r.L, r.L), dtype=torch.int8, device="cuda")
-                        r.draws = torch.empty(self.hpt * (r.L * r.L // 2), dtype=torch.int32,
+                        r.draws = torch.empty(hpt * (r.L * r.L // 2), dtype=torch.int32,
                                               device="cuda")
+                        sp, dp = r.spins.data_ptr(), r.draws.data_ptr()
+                        fill_tab[i] = (c.handle.value, dp, per, 0, 0, 0, 0)
+                        for colour in (0, 1):
+                            ising_tab[i, colour] = (sp, dp, r.L, colour, SHIFT[c.gen], self.t4,
+                                                    self.t8, per, 0)
+                        per_tab[i] = per
+                        half_total[i] = 2 * r.sweeps
+                        half_done[i] = 0
+                        r.numbers = r.sweeps * r.L * r.L
                         c.busy = r
-                        r.half_done = 0
-                        r.numbers = 0
-                        ising_tick(r, c)
-                        running.append(r)
+                        new_ising.append(i)
             pending = keep
-            if not fills:                       # nothing to launch now
-                future = realtime and nxt < len(reqs)
+            if new_ising:
+                running = np.concatenate([running, np.asarray(new_ising, np.int64)])
+            if not new_fills and not len(running):   # nothing to launch now
+                future = realtime and nxt < n_req
                 if inflight and not future:
                     retire(True)                # only completions can free slots or memory
                 elif future:
@@ -241,17 +243,40 @@ class Server:
                 elif not inflight and pending:
                     raise RuntimeError("a request does not fit the memory cap")
                 continue
-            sid = self.stream.cuda_stream
+            # One fill per running Ising request holding its next h half-sweeps'
+            # draws (row pitch h * per), then half-sweep t of every lattice reads
+            # column block t of its rows.
+            R = running
+            h = np.minimum(hpt, half_total[R] - half_done[R])
+            fills = fill_tab[R]
+            fills["n_per_stream"] = h * per_tab[R]
+            steps = []
+            for t in range(hpt):
+                m = h > t
+                if not m.any():
+                    break
+                Rt = R[m]
+                st = ising_tab[Rt, (half_done[Rt] + t) & 1]
+                if hpt > 1:
+                    st["d_draws"] += (4 * t * per_tab[Rt]).astype(np.uint64)
+                    st["pitch"] = np.where(h[m] > 1, h[m] * per_tab[Rt], 0)
+                steps.append(st)
+            half_done[R] += h
+            done_mask = half_done[R] == half_total[R]
+            if new_fills:
+                fills = np.concatenate([fill_tab[np.asarray(new_fills, np.int64)], fills])
             prng_batcher_launch(self.batcher, fills, sid)
-            for step in steps:                 # half-sweep t of every running lattice
-                prng_ising_half_sweep(step, sid)
+            for st in steps:                   # half-sweep t of every running lattice
+                prng_ising_half_sweep(st, sid)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(self.stream)
+            for i in R[done_mask]:
+                r = reqs[int(i)]
+                r.half_done = int(half_done[i])
+                self.clients[r.client].busy = None
+                finishing.append(r)
             inflight.append((ev, finishing))
-            for r in finishing:
-                if r.kind == "ising":
-                    self.clients[r.client].busy = None
-            running = [r for r in running if r.half_done < 2 * r.sweeps]
+            running = R[~done_mask]
         self.stream.synchronize()
         return reqs
 

@@ -71,6 +71,41 @@ def test_several_lattices_in_one_launch():
         np.testing.assert_array_equal(a.cpu().numpy(), w)
 
 
+@pytest.mark.parametrize("colour", [0, 1])
+def test_vector_and_scalar_forms_in_one_call(colour):
+    # L multiple of 16 takes the 16-site vector form, the others the scalar
+    # form; pitched draw rows (per % 8 == 0) stay on the vector form.
+    t4, t8 = P.prng_ising_thresholds(0.25)
+    rng = np.random.default_rng(11 + colour)
+    cases = [(16, 0, 0), (48, 0, 0), (256, 0, 0), (1024, 64, 3 * 64), (96, 72, 2 * 72),
+             (34, 0, 0), (64, 2, 6), (130, 0, 0)]
+    lat, bufs, reqs, want = [], [], [], []
+    for L, per, pitch in cases:
+        s = rng.choice(np.array([-1, 1], dtype=np.int8), size=(L, L))
+        n = L * L // 2
+        if pitch:
+            rows = n // per
+            buf = rng.integers(0, 2**32, size=rows * pitch, dtype=np.uint64).astype(np.uint32)
+            k = np.arange(n)
+            d = buf[(k // per) * pitch + k % per]
+        else:
+            buf = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+            d = buf
+        a = torch.from_numpy(s.copy()).cuda()
+        b = torch.from_numpy(buf.view(np.int32).copy()).cuda()
+        lat.append(a)
+        bufs.append(b)
+        reqs.append({"d_spins": a, "d_draws": b, "L": L, "colour": colour, "gen": "xor128",
+                     "t4": t4, "t8": t8, "per": per, "pitch": pitch})
+        w = s.copy()
+        oracle.ising_half_sweep(w, d, "xor128", colour, t4, t8)
+        want.append(w)
+    P.prng_ising_half_sweep(reqs)
+    torch.cuda.synchronize()
+    for a, w, c in zip(lat, want, cases):
+        np.testing.assert_array_equal(a.cpu().numpy(), w, err_msg=str(c))
+
+
 def test_ising_rejects_bad_lattices():
     d = torch.empty(8, dtype=torch.int32, device="cuda")
     s = torch.ones((4, 4), dtype=torch.int8, device="cuda")
