@@ -268,6 +268,7 @@ int prng_ising_fused(prng_state* st, int8_t* d_spins, uint32_t L, uint32_t colou
   q.shift = kShift[st->gen];
   q.t4 = t4;
   q.t8 = t8;
+  q.vec4 = (L % 8 == 0 && (reinterpret_cast<uintptr_t>(d_spins) & 7) == 0) ? 1u : 0u;
   const Tile t = default_tile(st->gen, st->p);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;

@@ -58,6 +58,7 @@ struct IsingSink {
   uint32_t colour;     // sites with (x + y) % 2 == colour
   uint32_t shift;      // 24-bit acceptance value = draw >> shift
   uint32_t t4, t8;     // integer thresholds for dE = 4 and dE = 8
+  uint32_t vec4;       // L % 8 == 0 and spins 8-byte aligned: 4 aligned ranks as one 8-byte chunk
 };
 
 // One fill (or skip, or jump fill) as the kernels see it.
@@ -245,15 +246,58 @@ __device__ __forceinline__ void ising_site(const IsingSink& q, uint32_t k, uint3
   if (dE <= 0 || (dE == 4 ? r < q.t4 : r < q.t8)) row[x] = (int8_t)(-s);
 }
 
+// The same update of the four sites of colour ranks k .. k+3, k % 4 == 0,
+// with L % 8 == 0: they lie in one row at bytes xb .. xb+7 (xb = 2 (k - y L/2),
+// a multiple of 8), every other byte, so the row chunk and the chunks above
+// and below are single 8-byte loads, one byte beside the chunk completes the
+// neighbours, and the chunk goes back as one 8-byte store.  The store also
+// rewrites the chunk's other-colour bytes with the values it read; nothing
+// changes them during the half-sweep.
+__device__ __forceinline__ void ising_site4(const IsingSink& q, uint32_t k, uint4 v) {
+  const uint32_t L = q.L, half = q.half;
+  const uint32_t y = q.lg_half < 32 ? k >> q.lg_half : k / half;
+  const uint32_t xb = 2 * (k - y * half);
+  const uint32_t par = (y + q.colour) & 1u;
+  const uint32_t yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+  int8_t* row = q.spins + (uint64_t)y * L;
+  union B8 { uint2 v; int8_t c[8]; };
+  B8 C, U, D;
+  C.v = *reinterpret_cast<const uint2*>(row + xb);
+  U.v = *reinterpret_cast<const uint2*>(q.spins + (uint64_t)yu * L + xb);
+  D.v = *reinterpret_cast<const uint2*>(q.spins + (uint64_t)yd * L + xb);
+  const int side = par ? row[xb + 8 == L ? 0 : xb + 8] : row[xb == 0 ? L - 1 : xb - 1];
+  const uint32_t dr[4] = {v.x, v.y, v.z, v.w};
+  B8 O = C;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+      if ((uint32_t)p != par) continue;
+      const int bi = 2 * i + p;
+      const int s = C.c[bi];
+      const int l = bi == 0 ? side : C.c[bi - 1];
+      const int r = bi == 7 ? side : C.c[bi + 1];
+      const int dE = 2 * s * (U.c[bi] + D.c[bi] + l + r);
+      const uint32_t a = dr[i] >> q.shift;
+      if (dE <= 0 || (dE == 4 ? a < q.t4 : a < q.t8)) O.c[bi] = (int8_t)(-s);
+    }
+  }
+  *reinterpret_cast<uint2*>(row + xb) = O.v;
+}
+
 // Output of four consecutive draws (element index e of the first, at p) or
 // of one: stored, or consumed by the fused half-sweep.
 template <int OM, int WB>
 __device__ __forceinline__ void put4(const FillDesc& d, uint32_t* p, uint64_t e, uint4 v) {
   if constexpr (OM == OUT_ISING) {
-    ising_site(d.ising, (uint32_t)e, v.x);
-    ising_site(d.ising, (uint32_t)e + 1, v.y);
-    ising_site(d.ising, (uint32_t)e + 2, v.z);
-    ising_site(d.ising, (uint32_t)e + 3, v.w);
+    if (d.ising.vec4 && (e & 3) == 0) {
+      ising_site4(d.ising, (uint32_t)e, v);
+    } else {
+      ising_site(d.ising, (uint32_t)e, v.x);
+      ising_site(d.ising, (uint32_t)e + 1, v.y);
+      ising_site(d.ising, (uint32_t)e + 2, v.z);
+      ising_site(d.ising, (uint32_t)e + 3, v.w);
+    }
   } else {
     st_chunk<OM, WB>(p, v);
   }
@@ -387,20 +431,34 @@ struct RowFlusher {
   __device__ __forceinline__ void flush(uint64_t g0, int w) const {
     if constexpr (OM == OUT_ISING) {
       // The fused half-sweep: every staged draw updates its site.  The
-      // CTA's threads take the tile's elements in row order (consecutive
-      // threads, consecutive colour ranks), stepping (row, column) by T
-      // elements without a division per element.
-      const int qT = T / w, rT = T - qT * w;
-      int r = threadIdx.x / w, c = threadIdx.x - r * w;
-      for (int i = threadIdx.x; i < T * w; i += T) {
+      // CTA's threads take the tile's elements in row order, four at a time
+      // (consecutive threads, consecutive quads of colour ranks: one 8-byte
+      // chunk of a lattice row each when the ranks are 4-aligned), stepping
+      // (row, quad) by T quads without a division per quad; the columns
+      // past the last whole quad go one at a time.
+      const int wq = w >> 2;
+      if (wq > 0) {
+        const int qT = T / wq, rT = T - qT * wq;
+        int r = threadIdx.x / wq, c = threadIdx.x - r * wq;
+        for (int i = threadIdx.x; i < T * wq; i += T) {
+          if (irow0 + r < irows) {
+            const uint32_t e = (uint32_t)((irow0 + r) * ipitch + g0) + (uint32_t)(4 * c);
+            const uint32_t* t = tile + r * SPW + 4 * c;
+            put4<OUT_ISING, WB>(*dp, nullptr, e, make_uint4(t[0], t[1], t[2], t[3]));
+          }
+          r += qT;
+          c += rT;
+          if (c >= wq) {
+            c -= wq;
+            r++;
+          }
+        }
+      }
+      const int wr = w - 4 * wq;
+      for (int i = threadIdx.x; i < T * wr; i += T) {
+        const int r = i / wr, c = 4 * wq + (i - r * wr);
         if (irow0 + r < irows)
           ising_site(dp->ising, (uint32_t)((irow0 + r) * ipitch + g0) + (uint32_t)c, tile[r * SPW + c]);
-        r += qT;
-        c += rT;
-        if (c >= w) {
-          c -= w;
-          r++;
-        }
       }
     } else {
       switch ((uint32_t)(0u - (uint32_t)g0) & 3u) {
