@@ -255,7 +255,11 @@ typedef struct prng_ising_req {
 } prng_ising_req;
 
 /* One half-sweep of each of the n lattices, asynchronously on `stream`.
- * The descriptors are passed by value to the kernels (no allocation). */
+ * The descriptors are passed by value to the kernels (no allocation).
+ * Lattices with L a multiple of 16, d_spins and d_draws 16-byte aligned and
+ * (pitch = 0 or per a multiple of 8 and pitch of 4) run a thread per 16
+ * sites with 16-byte row and draw accesses; the others a thread per site.
+ * The result is the same. */
 int prng_ising_half_sweep(const prng_ising_req *reqs, uint32_t n, void *stream);
 
 /* Fused half-sweep (the paper's "virtualised" generator, Section 3.1: draws
@@ -266,7 +270,9 @@ int prng_ising_half_sweep(const prng_ising_req *reqs, uint32_t n, void *stream);
  * lattice ends bit-identical to prng_fill_u32 of that block followed by
  * prng_ising_half_sweep with the generator's shift (7 for GGL and RANECU, 8
  * for XOR128 and MT19937, 0 for RANMAR and RANLUX).  L even, 2 <= L <=
- * 65534, L*L/2 a multiple of n_streams (PRNG_ESIZE otherwise). */
+ * 65534, L*L/2 a multiple of n_streams (PRNG_ESIZE otherwise).  With L a
+ * multiple of 8 and d_spins 8-byte aligned, four 4-aligned colour ranks
+ * update as one 8-byte chunk of their row. */
 int prng_ising_fused(prng_state *st, int8_t *d_spins, uint32_t L, uint32_t colour, uint32_t t4,
                      uint32_t t8, void *stream);
 
