@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import argparse
 
+import numpy as np
 import torch
 
 from . import ISING_REQ_DTYPE, prng_ising_half_sweep, prng_ising_thresholds
@@ -32,7 +33,6 @@ def main(argv=None):
                            generator=g) for _ in range(a.n_lattices)]
     # descriptor rows built once, in the library's struct layout, so a timed
     # launch carries no per-lattice host work
-    import numpy as np
     reqs = np.zeros(a.n_lattices, ISING_REQ_DTYPE)
     for i, (s, d) in enumerate(zip(lat, draws)):
         reqs[i] = (s.data_ptr(), d.data_ptr(), a.L, 0, 8, t4, t8, 0, 0)
