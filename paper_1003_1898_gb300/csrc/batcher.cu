@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/prng.h"
 #include "batch.cuh"
@@ -41,6 +42,7 @@ struct prng_batcher {
   uint64_t max_items = 0;
   Slot slot[kSlots];
   int next = 0;
+  std::vector<const prng_state*> handles;   // duplicate check, sized once
 };
 
 namespace {
@@ -71,6 +73,12 @@ int prng_batcher_create(prng_batcher** out, uint32_t max_requests, uint64_t max_
   if (b == nullptr) return PRNG_EALLOC;
   b->max_requests = max_requests;
   b->max_items = max_items;
+  try {
+    b->handles.reserve(max_requests);
+  } catch (...) {
+    delete b;
+    return PRNG_EALLOC;
+  }
   for (auto& u : b->slot) {
     if (cudaMallocHost(&u.h_reqs, max_requests * sizeof(BatchReq)) != cudaSuccess ||
         cudaMallocHost(&u.h_items, max_items * sizeof(BatchItem)) != cudaSuccess ||
@@ -116,10 +124,12 @@ int prng_batcher_launch(prng_batcher* b, const prng_fill_req* reqs, uint32_t n_r
     total += fam_n[f];
   }
   if (total > b->max_items) return PRNG_ESIZE;
-  // A handle may appear once per launch (its streams advance once).
-  for (uint32_t i = 0; i < n_reqs; i++)
-    for (uint32_t j = i + 1; j < n_reqs; j++)
-      if (reqs[i].st == reqs[j].st) return PRNG_EBLOB;
+  // A handle may appear once per launch (its streams advance once): sorted
+  // copy of the handles, adjacent equal ones rejected.
+  b->handles.clear();
+  for (uint32_t i = 0; i < n_reqs; i++) b->handles.push_back(reqs[i].st);
+  std::sort(b->handles.begin(), b->handles.end());
+  if (std::adjacent_find(b->handles.begin(), b->handles.end()) != b->handles.end()) return PRNG_EBLOB;
 
   Slot& u = b->slot[b->next];
   if (u.pending) {

@@ -132,3 +132,37 @@ def test_batch_rejects_duplicate_handle():
         assert e.value.code == -8
     finally:
         P.prng_destroy(h)
+
+
+def test_batcher_launches_continue_streams_and_reject_duplicates():
+    # The serving loop's batcher: repeated launches over resident handles
+    # continue every stream; a handle twice in one launch, or more requests
+    # than the batcher was sized for, is rejected before anything runs.
+    specs = [("ggl", 0), ("ranlux", 223), ("mt19937", 0), ("ranmar", 0)]
+    ns, per = 64, 40
+    handles = [P.prng_create(g, 900 + i, ns, lux) for i, (g, lux) in enumerate(specs)]
+    b = P.prng_batcher_create(4, 4096)
+    try:
+        outs = [[_alloc(ns * per, False) for _ in specs] for _ in range(2)]
+        for t in range(2):
+            P.prng_batcher_launch(b, [{"st": h, "d_out": o, "n_per_stream": per}
+                                      for h, o in zip(handles, outs[t])])
+        torch.cuda.synchronize()
+        for i, (g, lux) in enumerate(specs):
+            ref = oracle.fill(g, 900 + i, ns, 2 * per, luxury=lux)
+            for t in range(2):
+                got = _bits(outs[t][i], ns * per).reshape(ns, per)
+                np.testing.assert_array_equal(got, ref[:, t * per:(t + 1) * per], err_msg=g)
+        o = _alloc(ns * per, False)
+        with pytest.raises(P.PrngError) as e:
+            P.prng_batcher_launch(b, [{"st": handles[0], "d_out": o, "n_per_stream": per},
+                                      {"st": handles[0], "d_out": o, "n_per_stream": per}])
+        assert e.value.code == -8
+        with pytest.raises(P.PrngError) as e:
+            P.prng_batcher_launch(b, [{"st": h, "d_out": o, "n_per_stream": per}
+                                      for h in handles + [handles[0]]])
+        assert e.value.code == -3
+    finally:
+        P.prng_batcher_destroy(b)
+        for h in handles:
+            P.prng_destroy(h)
