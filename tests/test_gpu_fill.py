@@ -268,6 +268,28 @@ def test_zero_length_fill_is_noop():
     np.testing.assert_array_equal(got, oracle.fill("mt19937", 9, 8, 10))
 
 
+def test_fill_rejects_bad_sizes_before_launching():
+    # Host validation: sizes whose element count overflows 64 bits and
+    # misaligned outputs are rejected with nothing launched; the stream is
+    # unchanged afterwards.
+    h = P.prng_create("xor128", 5, 8, 0)
+    buf = torch.empty(64, dtype=torch.int32, device="cuda")
+    try:
+        for fn, n, ptr, code in [(P.prng_fill_u32, 2**62, buf.data_ptr(), -3),
+                                 (P.prng_fill_f32, 2**61 + 1, buf.data_ptr(), -3),
+                                 (P.prng_fill_f64, 2**63 + 1, buf.data_ptr(), -3),
+                                 (P.prng_fill_u32, 4, buf.data_ptr() + 2, -3),
+                                 (P.prng_fill_f64, 4, buf.data_ptr() + 4, -3),
+                                 (P.prng_fill_u32, 4, 0, -4)]:
+            with pytest.raises(P.PrngError) as err:
+                fn(h, ptr, n)
+            assert err.value.code == code, (fn.__name__, n)
+        got = u32(fill(h, 8, 10))
+    finally:
+        P.prng_destroy(h)
+    np.testing.assert_array_equal(got, oracle.fill("xor128", 5, 8, 10))
+
+
 # ------------------------------------------------------------ jump-ahead
 
 @pytest.mark.parametrize("gen", ["ggl", "ranecu", "xor128", "mt19937"])
