@@ -1,14 +1,15 @@
 // k_mt.cu -- MT19937 fill and skip (Section 3.7; Appendix A, "Mersenne
 // twister").
 //
-// One warp per stream, its 624-word table in shared memory.  The twist
-// X_{n+624} = X_{n+397} ^ (X_n^upper | X_{n+1}^lower) A is done in place in
-// five warp-wide chunks of 128 consecutive entries, in increasing order:
-// entry k reads old k and k+1 and either old k+397 (k < 227) or new k-227
-// (k >= 227, produced in an earlier chunk), so a chunk needs only a
-// __syncwarp between its reads and its writes.  Each new word is tempered
-// and stored by the lane that produced it: 32 lanes x 4 words are 512
-// consecutive bytes of the stream's row, written without staging.
+// A warp per stream (or half a warp, two streams per warp), its 624-word
+// table in shared memory.  The twist X_{n+624} = X_{n+397} ^ (X_n^upper |
+// X_{n+1}^lower) A is done in place in five chunks of 128 consecutive
+// entries, in increasing order: entry k reads old k and k+1 and either old
+// k+397 (k < 227) or new k-227 (k >= 227, produced in an earlier chunk), so
+// a chunk needs only a __syncwarp between its reads and its writes.  Each
+// new word is tempered and stored by the lane that produced it: a lane's 4
+// words are 16 bytes of a run of 512 (a warp) or 256 (a half) consecutive
+// bytes of the stream's row, written without staging.
 #include "batch.cuh"
 
 namespace prng {
