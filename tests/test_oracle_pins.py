@@ -507,3 +507,21 @@ def test_xor128_draws_from_state_continue_the_serial_sequence():
     np.testing.assert_array_equal(oracle.xor128_draws_from(st, 3000), ref)
     np.testing.assert_array_equal(oracle.xor128_draws_from(oracle.xor128_jump(st, 1234), 1766),
                                   ref[1234:])
+
+
+def _splitmix_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        for line in f:
+            if line.strip() and not line.lstrip().startswith("#"):
+                st, idx, val = line.split()
+                rows.append((int(st), int(idx), int(val)))
+    return rows
+
+
+@pytest.mark.parametrize("state,index,value", _splitmix_rows())
+def test_splitmix64_reference_outputs(state, index, value):
+    # Output i of the generator from `state` is the oracle's first output
+    # from state + (i - 1) gamma (the state advances by the gamma per call).
+    gamma = 0x9E3779B97F4A7C15
+    assert oracle.splitmix64((state + (index - 1) * gamma) % 2**64) == value
