@@ -17,10 +17,11 @@
  *   - f32 outputs are (v >> sh) * 2^-24 computed exactly, with sh = 7 for
  *     GGL/RANECU, 8 for XOR128/MT19937 and 0 for RANMAR/RANLUX.
  *
- * Parity pins live in tests/test_oracle_pins.py.  Two parts are only partly
+ * Parity pins live in tests/test_oracle_pins.py.  One part is only partly
  * pinned ("parity unpinned"): the RANECU combination step (each component is
- * pinned, the combination only by construction) and XOR128 (no printed known
- * answer; pinned by the paper's GF(2) matrix form and by linearity).
+ * pinned, the combination only by construction).  XOR128, which has no known
+ * answer in the paper, is pinned by its GF(2) matrix form, by linearity and
+ * by the outputs of Marsaglia's routine from its published initial state.
  */
 #ifndef PRNG_ORACLE_H
 #define PRNG_ORACLE_H

@@ -525,3 +525,20 @@ def test_splitmix64_reference_outputs(state, index, value):
     # from state + (i - 1) gamma (the state advances by the gamma per call).
     gamma = 0x9E3779B97F4A7C15
     assert oracle.splitmix64((state + (index - 1) * gamma) % 2**64) == value
+
+
+def _xor128_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "xor128_marsaglia.txt")) as f:
+        for line in f:
+            if line.strip() and not line.lstrip().startswith("#"):
+                x, y, z, w, idx, val = (int(t) for t in line.split())
+                rows.append(((x, y, z, w), idx, val))
+    return rows
+
+
+def test_xor128_known_answer_from_marsaglias_state():
+    rows = _xor128_rows()
+    assert rows
+    for state, idx, val in rows:
+        assert int(oracle.xor128_draws_from(state, idx)[-1]) == val, idx
