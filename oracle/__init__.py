@@ -6,8 +6,9 @@ Appendix A).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import it.  The library (``paper_1003_1898_gb300``)
 never imports it and shares no code with it.
 
-Parity unpinned (partially): the RANECU combination step; see the header
-of ``prng_oracle.h``.
+Every function is pinned to facts outside the oracle (tests/test_oracle_pins.py);
+the readings where the paper is silent are listed in the header of
+``prng_oracle.h``.
 """
 from __future__ import annotations
 

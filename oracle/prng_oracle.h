@@ -17,11 +17,14 @@
  *   - f32 outputs are (v >> sh) * 2^-24 computed exactly, with sh = 7 for
  *     GGL/RANECU, 8 for XOR128/MT19937 and 0 for RANMAR/RANLUX.
  *
- * Parity pins live in tests/test_oracle_pins.py.  One part is only partly
- * pinned ("parity unpinned"): the RANECU combination step (each component is
- * pinned, the combination only by construction).  XOR128, which has no known
- * answer in the paper, is pinned by its GF(2) matrix form, by linearity and
- * by the outputs of Marsaglia's routine from its published initial state.
+ * Parity pins live in tests/test_oracle_pins.py.  The RANECU combination
+ * step, for which no printed value exists, is pinned at the boundaries of
+ * its rule (equal components, differences of -1 and 1, components at their
+ * extremes; tests/golden/ranecu_combination.txt) and by the congruence
+ * Z = X1 - X2 (mod m1 - 1) with Z in [1, m1 - 1].  XOR128, which has no
+ * known answer in the paper, is pinned by its GF(2) matrix form, by
+ * linearity and by the outputs of Marsaglia's routine from its published
+ * initial state.
  */
 #ifndef PRNG_ORACLE_H
 #define PRNG_ORACLE_H
