@@ -39,6 +39,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 // Host-side staging of descriptors and items (pageable; a copy from it has
 // consumed the source when cudaMemcpyAsync returns).
 alignas(256) unsigned char g_host[kReqBytes + kItemBytes];
+// The handles of a call, sorted to find duplicates, and their positions
+// after the call, committed only once every copy and launch was enqueued.
+prng_state* g_sorted[kMaxRequests];
+uint32_t g_new_pos[kMaxRequests];
 std::mutex g_lock;
 
 // Device address of g_scratch, looked up once per device.
@@ -52,6 +56,9 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
   if (n_reqs == 0) return PRNG_OK;
   if (reqs == nullptr) return PRNG_ENULL;
   if (n_reqs > kMaxRequests) return PRNG_ESCRATCH;
+  // The static staging below is shared by every call: host threads take
+  // turns from here on.
+  std::lock_guard<std::mutex> guard(g_lock);
   // Validate and count items per family (no allocation).
   uint64_t fam_n[FAM_COUNT] = {};
   for (uint32_t i = 0; i < n_reqs; i++) {
@@ -60,8 +67,7 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
     if (r.n_per_stream > 0 && r.d_out == nullptr) return PRNG_ENULL;
     if ((reinterpret_cast<uintptr_t>(r.d_out) & 3) != 0) return PRNG_ESIZE;
     if (r.n_per_stream > 0 && r.st->n_streams > UINT64_MAX / r.n_per_stream) return PRNG_ESIZE;
-    for (uint32_t j = 0; j < i; j++)
-      if (reqs[j].st == r.st) return PRNG_EBLOB;
+    g_sorted[i] = r.st;
     if (r.reseed) fam_n[FAM_SEED] += (r.st->n_streams + 255) / 256;
     if (r.n_per_stream > 0) {
       const int f = fill_family(r.st->gen, r.st->p, r.f32 != 0);
@@ -76,10 +82,12 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
     total += fam_n[f];
   }
   if (total > kMaxItems) return PRNG_ESCRATCH;
+  // A handle may appear once per call (its streams advance once).
+  std::sort(g_sorted, g_sorted + n_reqs);
+  if (std::adjacent_find(g_sorted, g_sorted + n_reqs) != g_sorted + n_reqs) return PRNG_EBLOB;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PRNG_ECUDA;
-  std::lock_guard<std::mutex> guard(g_lock);
   if (g_dev_ptr[dev] == nullptr) {  // first call on this device: find the array's device address
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
@@ -95,7 +103,8 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
   BatchReq* h_reqs = reinterpret_cast<BatchReq*>(g_host);
   BatchItem* h_items = reinterpret_cast<BatchItem*>(g_host + kReqBytes);
 
-  // Descriptors (positions advance on the host, as for every fill) and items.
+  // Descriptors and items; the handles' new positions are kept aside until
+  // the whole pass has been enqueued.
   uint32_t fill_at[FAM_COUNT];
   std::memcpy(fill_at, fam_off, sizeof(fill_at));
   for (uint32_t i = 0; i < n_reqs; i++) {
@@ -116,7 +125,7 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
     q.seed = r.seed;
     q.gen = st->gen;
     q.reseed = r.reseed ? 1 : 0;
-    st->pos = advance_pos(st->gen, q.d.pos, r.n_per_stream);
+    g_new_pos[i] = advance_pos(st->gen, q.d.pos, r.n_per_stream);
     if (r.reseed)
       for (uint64_t r0 = 0; r0 < st->n_streams; r0 += 256)
         h_items[fill_at[FAM_SEED]++] =
@@ -164,5 +173,7 @@ extern "C" int prng_batch_fill_noalloc(const prng_fill_req* reqs, uint32_t n_req
       default: e = launch_batch_ranlux(q, lux_p_of(f), tile_of(f), f32, s); break;
     }
   }
-  return e == cudaSuccess ? PRNG_OK : PRNG_ECUDA;
+  if (e != cudaSuccess) return PRNG_ECUDA;
+  for (uint32_t i = 0; i < n_reqs; i++) reqs[i].st->pos = g_new_pos[i];
+  return PRNG_OK;
 }

@@ -8,10 +8,10 @@ scratch is a fixed device array inside the library.  Twin handles are
 filled by both entry points, twice in a row, and every output must be the
 same bytes.  This file is named so that pytest collects it last.
 """
-import ctypes
-
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,6 +66,17 @@ def test_noalloc_batch_equals_allocating_batch_two_calls():
             for (g, lux, ns, nper), oa, ob in zip(SPECS, a_out, b_out):
                 assert np.array_equal(oa.cpu().numpy().view(np.uint32), ob.cpu().numpy().view(np.uint32)), \
                     (g, lux, call)
+            # and both are the oracle's draws: call 0 continues each stream
+            # after its 13 skipped draws, call 1 re-seeds from 5001
+            for i, ((g, lux, ns, nper), oa, ra) in enumerate(zip(SPECS, a_out, a_req)):
+                seed, skip = (900 + i, 13) if call == 0 else (5001, 0)
+                ref = oracle.fill(g, seed, ns, nper, luxury=lux, skip=skip).reshape(-1)
+                if ra["f32"]:
+                    ref = oracle.to_f32(g, ref).view(np.uint32)
+                n = ra["n_valid"]
+                host = oa.cpu().numpy()
+                assert np.array_equal(host.view(np.uint32)[:n], ref[:n]), (g, lux, call)
+                assert np.all(host[n:] == -7), (g, lux, call, "wrote past n_valid")
         # the handles themselves advanced identically
         for ha, hb in zip(a_h, b_h):
             assert P.prng_get_state(ha) == P.prng_get_state(hb)
