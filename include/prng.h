@@ -279,6 +279,13 @@ int prng_ising_fused(prng_state *st, int8_t *d_spins, uint32_t L, uint32_t colou
 /* t4 = floor(2^24 exp(-4 beta)), t8 = floor(2^24 exp(-8 beta)), in double. */
 int prng_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8);
 
+/* The generator's float shift sh (the f32 output is (v >> sh) 2^-24 and the
+ * Ising acceptance value is v >> sh): 7 for GGL and RANECU (31-bit words),
+ * 8 for XOR128 and MT19937 (32-bit words), 0 for RANMAR and RANLUX (24-bit
+ * words).  PRNG_EGEN for an unknown generator, PRNG_ENULL for a NULL
+ * pointer. */
+int prng_float_shift(prng_gen_t gen, uint32_t *shift);
+
 /* Batched fill that allocates nothing (no counterpart in the paper; a
  * service of this library).  It is meant for callers that must not let a
  * library allocate device memory: code running under a framework's caching
@@ -303,10 +310,29 @@ int prng_ising_thresholds(double beta, uint32_t *t4, uint32_t *t8);
  *     threads are serialised by a lock around the host-side staging.
  *   - The host copy of the descriptors is pageable: the call returns once
  *     it has been handed to the device copy engine, which may wait for
- *     `stream` to drain first. */
+ *     `stream` to drain first.
+ *   - The handles' positions move only once every copy and launch of the
+ *     call has been enqueued; a call that returns an error leaves every
+ *     handle where it was (outputs may then be partly written). */
 #define PRNG_NOALLOC_MAX_REQUESTS 4096u
 #define PRNG_NOALLOC_MAX_ITEMS 131072u
 int prng_batch_fill_noalloc(const prng_fill_req *reqs, uint32_t n_reqs, void *stream);
+
+/* Measurement aid for the RANLUX roofline (no counterpart in the paper):
+ * runs the RANLUX kernels' own 24-step subtract-with-borrow chain (24
+ * subtract-with-borrow steps, 24 low-byte clears, 3 instructions moving the
+ * borrow in and out of the carry flag: 51 integer instructions; Appendix A,
+ * "AWC and SWB") `iters` times on each of `chains` (1, 2 or 4) independent
+ * 24-word rings per thread, in 128-thread blocks, one wave:
+ * ceil(warps_per_sm / 4) blocks per SM, or as many as fit when
+ * warps_per_sm = 0.  *ops receives the integer instructions the launch
+ * executes; d_sink (sink_words uint32 of device memory, at least one per
+ * thread launched, else PRNG_ESIZE) receives one checksum word per thread.
+ * Asynchronous on `stream`; time it with events to get the chain's
+ * throughput (many chains, full occupancy) or its latency (one chain, one
+ * warp per scheduler). */
+int prng_calib_swb(uint32_t chains, uint32_t warps_per_sm, uint32_t iters, uint32_t *d_sink,
+                   uint64_t sink_words, uint64_t *ops, void *stream);
 
 /* Launch tile used by fills of generator `gen` (for RANLUX: of luxury p)
  * on this process: threads per CTA, staged draws per thread per tile

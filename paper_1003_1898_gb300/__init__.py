@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         "prng_ising_fused": ([vp, vp, u32, u32, u32, u32, vp], ctypes.c_int),
         "prng_ising_thresholds": ([ctypes.c_double, ctypes.POINTER(u32), ctypes.POINTER(u32)],
                                   ctypes.c_int),
+        "prng_float_shift": ([ctypes.c_int, ctypes.POINTER(u32)], ctypes.c_int),
+        "prng_calib_swb": ([u32, u32, u32, vp, u64, ctypes.POINTER(u64), vp], ctypes.c_int),
         "prng_host_alloc": ([ctypes.POINTER(vp), ctypes.c_size_t], ctypes.c_int),
         "prng_host_free": ([vp], ctypes.c_int),
         "prng_destroy": ([vp], None),
@@ -299,7 +301,21 @@ def prng_batcher_destroy(b):
     lib().prng_batcher_destroy(b)
 
 
-SHIFT = {GGL: 7, RANECU: 7, XOR128: 8, MT19937: 8, RANMAR: 0, RANLUX: 0}
+def prng_float_shift(gen) -> int:
+    """The generator's float shift: f32 = (v >> sh) 2^-24, and v >> sh is
+    the Ising acceptance value."""
+    sh = ctypes.c_uint32()
+    _check(lib().prng_float_shift(_gen(gen), ctypes.byref(sh)), "prng_float_shift")
+    return sh.value
+
+
+def prng_calib_swb(chains: int, warps_per_sm: int, iters: int, sink, stream=None) -> int:
+    """Launch the subtract-with-borrow calibration kernel; returns the integer
+    instructions it executes (time the launch with events)."""
+    ops = ctypes.c_uint64()
+    _check(lib().prng_calib_swb(chains, warps_per_sm, iters, _ptr(sink), sink.numel(),
+                                ctypes.byref(ops), _stream(stream)), "prng_calib_swb")
+    return ops.value
 
 
 def prng_ising_thresholds(beta: float):
@@ -326,7 +342,7 @@ def prng_ising_half_sweep(reqs, stream=None):
         arr[i].d_draws = _ptr(r["d_draws"])
         arr[i].L = r["L"]
         arr[i].colour = r["colour"]
-        arr[i].shift = r["shift"] if "shift" in r else SHIFT[_gen(r["gen"])]
+        arr[i].shift = r["shift"] if "shift" in r else prng_float_shift(r["gen"])
         arr[i].t4 = r["t4"]
         arr[i].t8 = r["t8"]
         arr[i].per = r.get("per", 0)

@@ -238,13 +238,24 @@ int prng_fill_f64(prng_state* st, double* d_out, uint64_t n_per_stream, void* st
   return fill_impl(st, d_out, n_per_stream, OUT_F64, static_cast<cudaStream_t>(stream));
 }
 
+// The shift that leaves a draw's 24 top significant bits (reading R7): 31-bit
+// GGL and RANECU words lose 7 bits, 32-bit XOR128 and MT19937 words 8, the
+// 24-bit RANMAR and RANLUX words none.
+static const uint32_t kFloatShift[6] = {7, 8, 7, 0, 0, 8};
+
+int prng_float_shift(prng_gen_t gen, uint32_t* shift) {
+  if (shift == nullptr) return PRNG_ENULL;
+  if ((int)gen < 0 || (int)gen > 5) return PRNG_EGEN;
+  *shift = kFloatShift[gen];
+  return PRNG_OK;
+}
+
 int prng_ising_fused(prng_state* st, int8_t* d_spins, uint32_t L, uint32_t colour, uint32_t t4,
                      uint32_t t8, void* stream) {
   if (st == nullptr || d_spins == nullptr) return PRNG_ENULL;
   if (L < 2 || (L & 1) != 0 || L > 65534 || colour > 1) return PRNG_ESIZE;
   const uint64_t sites = (uint64_t)L * (L / 2);
   if (sites % st->n_streams != 0) return PRNG_ESIZE;
-  static const uint32_t kShift[6] = {7, 8, 7, 0, 0, 8};   // 24-bit value of a draw
   FillDesc d{};
   d.state = st->d_state;
   d.n_rows = st->n_streams;
@@ -265,7 +276,7 @@ int prng_ising_fused(prng_state* st, int8_t* d_spins, uint32_t L, uint32_t colou
     for (uint32_t b = 0; b < 32; b++)
       if ((1u << b) == q.half) q.lg_half = b;
   q.colour = colour;
-  q.shift = kShift[st->gen];
+  q.shift = kFloatShift[st->gen];
   q.t4 = t4;
   q.t8 = t8;
   q.vec4 = (L % 8 == 0 && (reinterpret_cast<uintptr_t>(d_spins) & 7) == 0) ? 1u : 0u;

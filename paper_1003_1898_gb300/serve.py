@@ -27,9 +27,9 @@ import collections
 import dataclasses
 import time
 
-from . import (FILL_REQ_DTYPE, GEN_IDS, ISING_REQ_DTYPE, SHIFT, prng_batcher_create,
+from . import (FILL_REQ_DTYPE, GEN_IDS, ISING_REQ_DTYPE, prng_batcher_create,
                prng_batcher_destroy, prng_batcher_launch, prng_create, prng_destroy, prng_info,
-               prng_ising_half_sweep, prng_ising_thresholds)
+               prng_float_shift, prng_ising_half_sweep, prng_ising_thresholds)
 
 ISING_BETA = 0.4406868
 
@@ -61,6 +61,7 @@ class Client:
         self.n_streams = n_streams
         self.handle = prng_create(self.gen, seed, n_streams, luxury)
         self.state_bytes = prng_info(self.handle)["state_bytes"]
+        self.shift = prng_float_shift(self.gen)   # 24-bit acceptance value = draw >> shift
         self.busy = None           # running Ising request
 
     def close(self):
@@ -221,7 +222,7 @@ class Server:
                         sp, dp = r.spins.data_ptr(), r.draws.data_ptr()
                         fill_tab[i] = (c.handle.value, dp, per, 0, 0, 0, 0)
                         for colour in (0, 1):
-                            ising_tab[i, colour] = (sp, dp, r.L, colour, SHIFT[c.gen], self.t4,
+                            ising_tab[i, colour] = (sp, dp, r.L, colour, c.shift, self.t4,
                                                     self.t8, per, 0)
                         per_tab[i] = per
                         half_total[i] = 2 * r.sweeps
