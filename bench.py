@@ -319,25 +319,36 @@ def max_over_ranks(value: float, dist, device) -> float:
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm.  Every item of the GPU step has the
+    same count (2^30 numbers), so a step here is the same mix scaled down:
+    each item draws `cpu_sample` numbers.  ms_per_step is that sampled
+    step's own wall time, and value is the numbers it drew over that time."""
     if rank != 0:
         return
     sample = args.cpu_sample
+    items = step_items()
+    assert len({n for *_, n in items}) == 1, "the sample assumes equal item counts"
+    per_step = sample * len(items)
     steps_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        rate, _ = cpu_oracle_rate(sample)
+        cpu_oracle_rate(sample)
         if i >= args.warmup:
-            steps_t.append((time.perf_counter() - t0, rate))
-    rate = statistics.median(r for _, r in steps_t)
-    ms = 1e3 * numbers_per_step() / rate
+            steps_t.append(time.perf_counter() - t0)
+    secs = statistics.median(steps_t)
+    rate = per_step / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "numbers/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "sample": f"each step is the workload's mix scaled down: {sample} numbers per "
+                             f"step item ({len(items)} items, {per_step} numbers per step); "
+                             "ms_per_step is that step's own time",
+                   "numbers_per_step": per_step},
         "cpu_baseline": {"value": rate, "unit": "numbers/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} draws per step item, single thread, scaled to "
-                                   "the step's mix"},
+                         "sample": f"{sample} draws per step item, single thread"},
         "e2e": {"value": rate, "unit": "numbers/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -347,7 +358,7 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------ GPU arm
 
 LUX_STREAMS, LUX_PER = 65536, 4096
-INT_LANES_PER_SM = 64      # 32-bit integer ALU lanes per SM per clock (half the FP32 rate)
+SWB_CHAIN_OPS = 24 * 2 + 3  # one 24-step chain: 24 subtract-with-borrow, 24 clears, 3 flag moves
 
 
 def _time_ms(torch, stream, fn, reps=5, warm=2):
@@ -447,18 +458,56 @@ def measure_f64(P, torch, out_u, handles, seed_r, stream):
     return res
 
 
+def measure_swb_rate(P, torch, dev, stream):
+    """The integer rate of the RANLUX kernels' own subtract-with-borrow chain,
+    measured (prng_calib_swb): throughput with four independent chains per
+    thread at full occupancy, and latency with one chain per thread and one
+    warp per scheduler (4 per SM).  Clocks are sampled during the timed
+    launches, so the rate is also given per SM per clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 2048, dtype=torch.int32, device=dev)
+    sid = stream.cuda_stream
+    res = {"sm_count": sms, "chain_instructions": SWB_CHAIN_OPS}
+    with clock_sampler(torch, dev, dev.index or 0) as clk:
+        for name, chains, warps, iters in (("throughput", 4, 0, 8192), ("throughput_2", 2, 0, 8192),
+                                           ("latency", 1, 4, 4096)):
+            ops = [0]
+
+            def run():
+                ops[0] = P.prng_calib_swb(chains, warps, iters, sink, sid)
+            ms = _time_ms(torch, stream, run, reps=5, warm=2)
+            res[name] = {"chains_per_thread": chains, "warps_per_sm": warps or "max",
+                         "iters": iters, "ms": ms, "ops": ops[0], "ops_per_s": ops[0] / (ms / 1e3)}
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or 2070.0
+    res["clocks"] = c
+    for name in ("throughput", "throughput_2", "latency"):
+        r = res[name]
+        r["ops_per_sm_clk"] = r["ops_per_s"] / (sms * mhz * 1e6)
+    # one warp per scheduler, one chain per thread: cycles per SWB step
+    lat = res["latency"]
+    lat["cycles_per_step"] = (lat["ms"] / 1e3) * mhz * 1e6 / (lat["iters"] * 24)
+    res["bound_ops_per_s"] = max(res["throughput"]["ops_per_s"], res["throughput_2"]["ops_per_s"])
+    return res
+
+
 def measure_luxury_sweep(P, torch, dev, stream, sm_mhz):
     """ns/number of RANLUX f32 fills (2^28 over 65,536 streams) for every
     standard p, and the fraction of the integer-pipe bound reached.  The
     bound counts the subtract-with-borrow chains alone: p/24 steps per
     delivered number, each one subtract-with-borrow plus one low-byte clear,
     plus 3 instructions per 24-step chain to move the borrow in and out of
-    the carry flag; the pipe retires INT_LANES_PER_SM lanes per SM per clock."""
+    the carry flag, at the rate that same chain is measured to run at on
+    this GPU with its latency hidden (measure_swb_rate)."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = sm_mhz or 2070.0
+    swb = measure_swb_rate(P, torch, dev, stream)
+    rate = swb["bound_ops_per_s"]
     out = torch.empty(LUX_STREAMS * LUX_PER, dtype=torch.float32, device=dev)
     res = {"workload": f"{LUX_STREAMS} streams x {LUX_PER} f32 per p (2^28 numbers)",
-           "sm_count": sms, "sm_mhz": mhz, "int_lanes_per_sm_clk": INT_LANES_PER_SM, "levels": {}}
+           "sm_count": sms, "sm_mhz": mhz, "swb_chain_rate": swb,
+           "bound_source": "measured: prng_calib_swb throughput (same chain, latency hidden)",
+           "levels": {}}
     for p in (24, 48, 97, 223, 389, 120, 240, 408):
         h = P.prng_create("ranlux", SEED, LUX_STREAMS, p)
         sid = stream.cuda_stream
@@ -475,8 +524,8 @@ def measure_luxury_sweep(P, torch, dev, stream, sm_mhz):
         P.prng_destroy(h)
         ms = statistics.median(ts)
         n = LUX_STREAMS * LUX_PER
-        instr = (p / 24.0) * (2.0 + 3.0 / 24.0)
-        bound_ms = 1e3 * n * instr / (sms * INT_LANES_PER_SM * mhz * 1e6)
+        instr = (p / 24.0) * SWB_CHAIN_OPS / 24.0
+        bound_ms = 1e3 * n * instr / rate
         hbm_ms = 1e3 * 4 * n / (peaks()[0] * 1e9)
         res["levels"][str(p)] = {"ms": ms, "ns_per_number": 1e6 * ms / n, "numbers_per_s": n / (ms / 1e3),
                                  "int_instr_per_number": instr, "int_bound_ms": bound_ms,
@@ -865,7 +914,120 @@ def measure_e2e(P, handles, seed_r, items, dev, args, rank=0):
                     "copy_engine_gbs is one 4 GiB device-to-pinned-host copy for context"}
 
 
+# ------------------------------------------------------------ single kernels
+
+def kernel_main(argv):
+    """One kernel in isolation (CUDA events), for tile studies and profiler
+    captures of a single launch:
+
+      bench.py kernel fill GEN {u32,f32,f64} N_STREAMS N_PER [--luxury P]
+          [--reps R] [--timed K] [--jump] [--skip] [--tile T,C,S]
+      bench.py kernel ising L N_LATTICES [--reps R] [--timed K]
+      bench.py kernel fused GEN L N_STREAMS [--luxury P] [--reps R] [--timed K]
+
+    fill: one fill of GEN (--jump: the single-sequence jump fill, N_STREAMS
+    chunks of N_PER draws; --skip: prng_skip of N_PER draws per stream; f64:
+    N_PER doubles per stream).  The tuned tiles are applied first, then
+    --tile for GEN.  ising: one batched half-sweep launch over N_LATTICES
+    cold-start lattices of side L with random draws (colour 0).  fused: one
+    fused half-sweep (prng_ising_fused) of a cold-start L x L lattice on a
+    handle of N_STREAMS streams.  Prints one line per timed call."""
+    import numpy as np
+    import torch
+
+    import paper_1003_1898_gb300 as P
+    from paper_1003_1898_gb300 import build as B
+    from paper_1003_1898_gb300 import tune
+    from paper_1003_1898_gb300.workloads import JUMP_X0 as JX0
+    ap = argparse.ArgumentParser(prog="bench.py kernel")
+    sub = ap.add_subparsers(dest="what", required=True)
+    f = sub.add_parser("fill")
+    f.add_argument("gen", choices=sorted(P.GEN_IDS))
+    f.add_argument("dtype", choices=["u32", "f32", "f64"])
+    f.add_argument("n_streams", type=int)
+    f.add_argument("n_per", type=int)
+    f.add_argument("--jump", action="store_true")
+    f.add_argument("--skip", action="store_true")
+    f.add_argument("--tile", default=None)
+    i = sub.add_parser("ising")
+    i.add_argument("L", type=int)
+    i.add_argument("n_lattices", type=int)
+    u = sub.add_parser("fused")
+    u.add_argument("gen", choices=sorted(P.GEN_IDS))
+    u.add_argument("L", type=int)
+    u.add_argument("n_streams", type=int)
+    for q in (f, i, u):
+        q.add_argument("--luxury", type=int, default=223)
+        q.add_argument("--reps", type=int, default=3, help="untimed calls before the timed ones")
+        q.add_argument("--timed", type=int, default=1, help="timed calls")
+    a = ap.parse_args(argv)
+    B.build()
+    P.lib()
+    tune.load_and_apply()
+    h = None
+    if a.what == "fill":
+        if a.tile:
+            P.prng_set_tile(a.gen, a.luxury if a.gen == "ranlux" else 0, *map(int, a.tile.split(",")))
+        n = a.n_streams * a.n_per
+        tdt = {"f32": torch.float32, "f64": torch.float64}.get(a.dtype, torch.int32)
+        out = None if a.skip else torch.empty(n, dtype=tdt, device="cuda")
+        if a.jump:
+            fj = P.prng_fill_jump_f32 if a.dtype == "f32" else P.prng_fill_jump_u32
+            call = lambda: fj(a.gen, JX0[a.gen], n, a.n_streams, out)
+        else:
+            h = P.prng_create(a.gen, SEED, a.n_streams, a.luxury)
+            fill = {"f32": P.prng_fill_f32, "f64": P.prng_fill_f64}.get(a.dtype, P.prng_fill_u32)
+            call = (lambda: P.prng_skip(h, a.n_per)) if a.skip else (lambda: fill(h, out, a.n_per))
+        what = (f"{a.gen} {a.dtype} {a.n_streams}x{a.n_per}{' jump' if a.jump else ''}"
+                f"{' skip' if a.skip else ''}")
+        unit = lambda ms: (f"{n / ms / 1e9:.3f} T/s  "
+                           f"{0.0 if a.skip else out.element_size() * n / ms / 1e6:.0f} GB/s")
+    elif a.what == "ising":
+        t4, t8 = P.prng_ising_thresholds(0.4406868)
+        g = torch.Generator(device="cuda").manual_seed(1)
+        lat = [torch.ones((a.L, a.L), dtype=torch.int8, device="cuda") for _ in range(a.n_lattices)]
+        draws = [torch.randint(-2**31, 2**31 - 1, (a.L * a.L // 2,), dtype=torch.int32,
+                               device="cuda", generator=g) for _ in range(a.n_lattices)]
+        # descriptor rows built once in the library's struct layout, so a
+        # timed launch carries no per-lattice host work
+        reqs = np.zeros(a.n_lattices, P.ISING_REQ_DTYPE)
+        for k, (sp, d) in enumerate(zip(lat, draws)):
+            reqs[k] = (sp.data_ptr(), d.data_ptr(), a.L, 0, 8, t4, t8, 0, 0)
+        call = lambda: P.prng_ising_half_sweep(reqs)
+        sites = a.n_lattices * a.L * a.L // 2
+        what = f"ising half-sweep {a.n_lattices} x L={a.L}"
+        unit = lambda ms: f"{sites / ms / 1e6:.1f} G site updates/s"
+    else:
+        t4, t8 = P.prng_ising_thresholds(0.4406868)
+        h = P.prng_create(a.gen, SEED, a.n_streams, a.luxury)
+        spins = torch.ones((a.L, a.L), dtype=torch.int8, device="cuda")
+        col = [0]
+
+        def call():
+            P.prng_ising_fused(h, spins, a.L, col[0], t4, t8)
+            col[0] ^= 1
+        sites = a.L * a.L // 2
+        what = f"fused half-sweep {a.gen} L={a.L} on {a.n_streams} streams"
+        unit = lambda ms: f"{sites / ms / 1e6:.1f} G site updates/s"
+    for _ in range(a.reps):
+        call()
+    torch.cuda.synchronize()
+    for _ in range(a.timed):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(f"{what}: {ms:.4f} ms  {unit(ms)}")
+    if h is not None:
+        P.prng_destroy(h)
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "kernel":
+        kernel_main(sys.argv[2:])
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
