@@ -834,30 +834,56 @@ def measure_serving(args):
     arrivals at each rate, requests 50/50 a fill of 1e3..1e6 numbers or 16
     checkerboard sweeps of an L x L Ising lattice (L in {256, 1024, 4096}),
     40 GB state + output cap.  Aggregate numbers/s counts every draw served
-    (fill outputs and Ising draws)."""
+    (fill outputs and Ising draws).  At every rate the same arrivals are
+    served twice: with continuous batching, and by a plain queue that runs
+    one request at a time (the one-launch-per-request baseline)."""
     from paper_1003_1898_gb300 import serve as S
     from paper_1003_1898_gb300 import workloads as W
     specs = W.serving_clients(W.SERVE_CLIENTS)
     out = {"clients": W.SERVE_CLIENTS, "streams_per_client": W.SERVE_STREAMS,
-           "mem_cap_bytes": W.SERVE_MEM_CAP, "rates": []}
+           "mem_cap_bytes": W.SERVE_MEM_CAP, "half_sweeps_per_tick": args.serve_hpt,
+           "rates": []}
+    arms = [a for a in ("continuous", "queue") if a in args.serve_arms]
     for rate in args.serve_rates:
         row = {"rate_per_s": rate, "requests": args.serve_requests}
-        for mode, max_active in (("continuous", 0), ("queue", 1)):
-            if mode == "queue" and rate != args.serve_rates[0]:
-                continue
-            raw = W.serving_requests(args.serve_requests, rate)
-            reqs = [S.Request(**r) for r in raw]
+        raw = W.serving_requests(args.serve_requests, rate)
+        for mode in arms:
             srv = S.Server(specs, n_streams=W.SERVE_STREAMS, mem_cap=W.SERVE_MEM_CAP,
-                           max_active=max_active)
+                           max_active=1 if mode == "queue" else 0,
+                           half_sweeps_per_tick=args.serve_hpt)
             try:
-                srv.run(reqs[: min(50, len(reqs))], realtime=False)   # warm-up (compile, caches)
-                reqs = [S.Request(**r) for r in raw]
-                done = srv.run(reqs, realtime=True)
+                srv.run([S.Request(**r) for r in raw[: min(50, len(raw))]],
+                        realtime=False)   # warm-up (compile, caches)
+                done = srv.run([S.Request(**r) for r in raw], realtime=True)
             finally:
                 srv.close()
             row[mode] = S.latency_stats(done)
         out["rates"].append(row)
     return out
+
+
+def serving_main(argv):
+    """The serving sweep alone: bench.py serving [--rates R ...] [--requests N]
+    [--arms continuous queue] [--hpt H].  Prints one JSON line."""
+    import torch
+    import paper_1003_1898_gb300 as P
+    from paper_1003_1898_gb300 import build as B
+    from paper_1003_1898_gb300 import tune
+    ap = argparse.ArgumentParser(prog="bench.py serving")
+    ap.add_argument("--rates", dest="serve_rates", type=float, nargs="+",
+                    default=[500.0, 1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 4000.0, 8000.0, 16000.0])
+    ap.add_argument("--requests", dest="serve_requests", type=int, default=10000)
+    ap.add_argument("--arms", dest="serve_arms", nargs="+", default=["continuous", "queue"])
+    ap.add_argument("--hpt", dest="serve_hpt", type=int, default=1)
+    a = ap.parse_args(argv)
+    B.build()
+    P.lib()
+    tune.load_and_apply()
+    dev = torch.device("cuda", 0)
+    with clock_sampler(torch, dev, 0) as clk:
+        res = measure_serving(a)
+    res["clocks"] = clk.summary()
+    print(json.dumps(res), flush=True)
 
 
 def measure_e2e(P, handles, seed_r, items, dev, args, rank=0):
@@ -1028,6 +1054,9 @@ def main():
     if len(sys.argv) > 1 and sys.argv[1] == "kernel":
         kernel_main(sys.argv[2:])
         return
+    if len(sys.argv) > 1 and sys.argv[1] == "serving":
+        serving_main(sys.argv[2:])
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -1040,8 +1069,10 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=20000)
     ap.add_argument("--batch-passes", type=int, default=3)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 4000.0, 16000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 2000.0, 4000.0, 16000.0])
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-arms", nargs="+", default=["continuous", "queue"])
+    ap.add_argument("--serve-hpt", type=int, default=1)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

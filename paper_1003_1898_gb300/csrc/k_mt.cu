@@ -9,7 +9,11 @@
 // a chunk needs only a __syncwarp between its reads and its writes.  Each
 // new word is tempered and stored by the lane that produced it: a lane's 4
 // words are 16 bytes of a run of 512 (a warp) or 256 (a half) consecutive
-// bytes of the stream's row, written without staging.
+// bytes of the stream's row, written without staging.  With half a warp per
+// stream, a lane keeps its own quads of the table in registers from one
+// 624-word block to the next (mt_blocks_reg), so the shared table serves
+// only the other lanes' lag reads; the kernel is bound by shared-memory
+// traffic and integer issue, not by the arithmetic alone.
 #include "batch.cuh"
 
 namespace prng {
@@ -37,18 +41,62 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
   return f ^ (y >> 1) ^ ((0u - (y & 1u)) & 0x9908B0DFu);
 }
 
+// Temper the new quad v = X_k .. X_{k+3} and hand it to the output: o[k]
+// onwards (16-byte stores when vec; PARTIAL: only entries k < take), or the
+// fused half-sweep's sites e0 + k onwards.
+template <int OM, bool PARTIAL>
+__device__ __forceinline__ void mt_emit(uint4 v, int k, uint32_t* o, int take, bool vec,
+                                        const FillDesc* d, uint64_t e0) {
+  uint4 t;
+  t.x = mt_conv<OM>(mt_temper(v.x));
+  t.y = mt_conv<OM>(mt_temper(v.y));
+  t.z = mt_conv<OM>(mt_temper(v.z));
+  t.w = mt_conv<OM>(mt_temper(v.w));
+  if constexpr (OM == OUT_ISING) {   // e0 + k: element index of word k
+    if (!PARTIAL) {
+      put4<OM, 32>(*d, nullptr, e0 + k, t);
+    } else {
+      if (k < take) put1<OM>(*d, nullptr, e0 + k, t.x);
+      if (k + 1 < take) put1<OM>(*d, nullptr, e0 + k + 1, t.y);
+      if (k + 2 < take) put1<OM>(*d, nullptr, e0 + k + 2, t.z);
+      if (k + 3 < take) put1<OM>(*d, nullptr, e0 + k + 3, t.w);
+    }
+  } else if (!PARTIAL && vec) {
+    st_chunk<OM, 32>(o + k, t);
+  } else {
+    if constexpr (OM == OUT_F64) {   // take and the table offset are even
+      if (!PARTIAL || k < take) st_pair<32>(o + k, t.x, t.y);
+      if (!PARTIAL || k + 2 < take) st_pair<32>(o + k + 2, t.z, t.w);
+    } else {
+      if (!PARTIAL || k < take) st_out(o + k, t.x);
+      if (!PARTIAL || k + 1 < take) st_out(o + k + 1, t.y);
+      if (!PARTIAL || k + 2 < take) st_out(o + k + 2, t.z);
+      if (!PARTIAL || k + 3 < take) st_out(o + k + 3, t.w);
+    }
+  }
+}
+
+// Start of the four lag words of the quad at k (a multiple of 4), one word
+// before them: X_{k+397} (old) for k <= 224, X_{k-227} (already new) from
+// k = 228 on.  The quad at 224 takes old words 621..623 and new X_0, which
+// is the word after its lag quad; both forms start on a 16-byte boundary.
+__device__ __forceinline__ int mt_lag_base(int k) { return k <= 224 ? k + 396 : k - 228; }
+
 // One twist of a stream's table (Appendix A, "Mersenne twister"), in place,
 // by the LPS lanes that own the stream (32: a warp; 16: half a warp, the
 // warp's other half twisting another stream in step), in chunks of
 // 4 LPS QPL entries (five of 128 for both forms); lane u owns the QPL quads
-// k .. k+3, k = k0 + 4 LPS q + 4 u, read and written with 16-byte shared
-// accesses, so each lane has QPL independent quads between two syncs.  Any
-// chunk size up to 227 keeps the in-place order valid.  The lag X_{k+397} is old
-// for k < 227 and already replaced (X_{k-227}) from 227 on; both start one
-// word past a 16-byte boundary, so they come from two aligned 16-byte loads.
-// Only the lane holding k = 224..227 straddles the switch.  Each new word is
-// tempered and, if o != null, written to o[k] (16-byte stores when VEC);
-// PARTIAL: only entries k < take are written.
+// k .. k+3, k = k0 + 4 LPS q + 4 u, so each lane has QPL independent quads
+// between two syncs.  Any chunk size up to 227 keeps the in-place order
+// valid.  A quad needs its own four words and the next one, X_{k+4}, and
+// the four lag words (mt_lag_base), which are the last three of an aligned
+// 16-byte quad and the first word of the next one.  Each lane loads its own
+// quad and its aligned lag quad with one 16-byte shared load each; the two
+// words after them are the first words that lane u+1 loaded, passed on by a
+// shuffle (the group's last lane takes lane 0's next row, and in the last
+// row loads them itself).  Each new word is tempered and, if o != null,
+// written to o[k] (16-byte stores when VEC); PARTIAL: only entries k < take
+// are written.
 template <int OM, bool PARTIAL, int LPS = 32, int QPL = 1>
 __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int take, bool vec,
                                          const FillDesc* d = nullptr, uint64_t e0 = 0) {
@@ -60,23 +108,41 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
     uint32_t b[QPL];
 #pragma unroll
     for (int q = 0; q < QPL; q++) {
-      const int k = k0 + 4 * LPS * q + 4 * lane;
+      const int kr = k0 + 4 * LPS * q;     // first quad of the row
+      const int k = kr + 4 * lane;
       a[q] = make_uint4(0, 0, 0, 0);
       f[q] = a[q];
-      b[q] = 0;
       if (k < 624) {
         a[q] = *reinterpret_cast<const uint4*>(s + k);
-        b[q] = s[k + 4 == 624 ? 0 : k + 4];
-        const bool old_lag = (k0 + CH <= 227) || (k0 < 227 && k + 3 < 227);
-        const bool new_lag = (k0 >= 227) || k >= 227;
-        if (old_lag || new_lag) {
-          const int base = old_lag ? k + 396 : k - 228;
-          const uint4 q1 = *reinterpret_cast<const uint4*>(s + base);
-          const uint32_t q2 = s[base + 4];
-          f[q] = make_uint4(q1.y, q1.z, q1.w, q2);
-        } else {  // k = 224: lags 621, 622, 623 (old) and 0 (new)
-          f[q] = make_uint4(s[621], s[622], s[623], s[0]);
-        }
+        // compile-time base when the whole row is on one side of 224 / 228
+        const int base = kr + 4 * LPS - 4 <= 224 ? k + 396 : (kr >= 228 ? k - 228 : mt_lag_base(k));
+        f[q] = *reinterpret_cast<const uint4*>(s + base);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < QPL; q++) {
+      uint32_t na = a[q].x, nf = f[q].x;
+      if (q + 1 < QPL && lane == 0) {        // lane LPS-1 reads lane 0: the next row
+        na = a[q + 1].x;
+        nf = f[q + 1].x;
+      }
+      b[q] = __shfl_sync(0xFFFFFFFFu, na, (lane + 1) & (LPS - 1), LPS);
+      const uint32_t h = __shfl_sync(0xFFFFFFFFu, nf, (lane + 1) & (LPS - 1), LPS);
+      f[q] = make_uint4(f[q].y, f[q].z, f[q].w, h);
+    }
+    {
+      const int kn = k0 + CH;                // the quad after the chunk (old)
+      if (kn < 624 && lane == LPS - 1) {
+        b[QPL - 1] = s[kn];
+        f[QPL - 1].w = s[mt_lag_base(kn)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < QPL; q++) {          // the table's last quad: X_624 is the new X_0
+      const int kr = k0 + 4 * LPS * q;
+      if (kr <= 620 && 620 < kr + 4 * LPS && 4 * lane + kr == 620) {
+        b[q] = s[0];
+        f[q].w = s[mt_lag_base(624)];
       }
     }
     __syncwarp();
@@ -90,37 +156,92 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
       v.z = mt_mix(a[q].z, a[q].w, f[q].z);
       v.w = mt_mix(a[q].w, b[q], f[q].w);
       *reinterpret_cast<uint4*>(s + k) = v;
-      if (o != nullptr) {
-        uint4 t;
-        t.x = mt_conv<OM>(mt_temper(v.x));
-        t.y = mt_conv<OM>(mt_temper(v.y));
-        t.z = mt_conv<OM>(mt_temper(v.z));
-        t.w = mt_conv<OM>(mt_temper(v.w));
-        if constexpr (OM == OUT_ISING) {   // e0 + k: element index of word k
-          if (!PARTIAL) {
-            put4<OM, 32>(*d, nullptr, e0 + k, t);
-          } else {
-            if (k < take) put1<OM>(*d, nullptr, e0 + k, t.x);
-            if (k + 1 < take) put1<OM>(*d, nullptr, e0 + k + 1, t.y);
-            if (k + 2 < take) put1<OM>(*d, nullptr, e0 + k + 2, t.z);
-            if (k + 3 < take) put1<OM>(*d, nullptr, e0 + k + 3, t.w);
-          }
-        } else if (!PARTIAL && vec) {
-          st_chunk<OM, 32>(o + k, t);
-        } else {
-          if constexpr (OM == OUT_F64) {   // take and the table offset are even
-            if (!PARTIAL || k < take) st_pair<32>(o + k, t.x, t.y);
-            if (!PARTIAL || k + 2 < take) st_pair<32>(o + k + 2, t.z, t.w);
-          } else {
-            if (!PARTIAL || k < take) st_out(o + k, t.x);
-            if (!PARTIAL || k + 1 < take) st_out(o + k + 1, t.y);
-            if (!PARTIAL || k + 2 < take) st_out(o + k + 2, t.z);
-            if (!PARTIAL || k + 3 < take) st_out(o + k + 3, t.w);
-          }
-        }
-      }
+      if (o != nullptr) mt_emit<OM, PARTIAL>(v, k, o, take, vec, d, e0);
     }
     __syncwarp();
+  }
+}
+
+// Whole 624-word blocks of a fill, with each lane's own quads of the table
+// held in registers from block to block (lane u owns the quads k = CH c +
+// 4 LPS q + 4 u of every block, so after a twist its new quads are the old
+// ones of the next block).  The table in shared memory is kept as a mirror:
+// every new quad is stored there too, for the other lanes' lag reads, so
+// the only shared load of a quad is its aligned lag quad (mt_lag_base).  The
+// word after a quad and the word after its lag quad come from lane u+1 by a
+// shuffle; the group's last lane takes lane 0's next row (of the next chunk,
+// for the chunk's last row, whose lag word it loads), and the table's last
+// quad, whose next word is the new X_0, loads both.
+template <int OM, int LPS, int QPL>
+__device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o, uint64_t nb,
+                                              bool vec, const FillDesc* d, uint64_t e0) {
+  constexpr int CH = 4 * LPS * QPL, NCH = (624 + CH - 1) / CH;
+  static_assert(CH <= 227, "a chunk may not reach its own lags");
+  static_assert((LPS & (LPS - 1)) == 0, "lane u+1 is taken modulo a power of two");
+  uint4 A[NCH][QPL];
+#pragma unroll
+  for (int c = 0; c < NCH; c++)
+#pragma unroll
+    for (int q = 0; q < QPL; q++) {
+      const int k = c * CH + 4 * LPS * q + 4 * lane;
+      A[c][q] = k < 624 ? *reinterpret_cast<const uint4*>(s + k) : make_uint4(0, 0, 0, 0);
+    }
+  for (uint64_t blk = 0; blk < nb; blk++) {
+    uint32_t* ob = o != nullptr ? o + blk * 624 : nullptr;
+    const uint64_t eb = e0 + blk * 624;
+#pragma unroll
+    for (int c = 0; c < NCH; c++) {
+      const int k0 = c * CH;
+      uint4 F[QPL];
+#pragma unroll
+      for (int q = 0; q < QPL; q++) {
+        const int kr = k0 + 4 * LPS * q, k = kr + 4 * lane;
+        F[q] = make_uint4(0, 0, 0, 0);
+        if (k < 624) {
+          const int base = kr + 4 * LPS - 4 <= 224 ? k + 396 : (kr >= 228 ? k - 228 : mt_lag_base(k));
+          F[q] = *reinterpret_cast<const uint4*>(s + base);
+        }
+      }
+      uint32_t b[QPL], h[QPL];
+#pragma unroll
+      for (int q = 0; q < QPL; q++) {
+        uint32_t na = A[c][q].x, nf = F[q].x;
+        if (lane == 0) {
+          if (q + 1 < QPL) {
+            na = A[c][q + 1].x;
+            nf = F[q + 1].x;
+          } else if (c + 1 < NCH) {
+            na = A[c + 1][0].x;          // still the old word: chunk c+1 comes later
+          }
+        }
+        b[q] = __shfl_sync(0xFFFFFFFFu, na, (lane + 1) & (LPS - 1), LPS);
+        h[q] = __shfl_sync(0xFFFFFFFFu, nf, (lane + 1) & (LPS - 1), LPS);
+      }
+      if (k0 + CH < 624 && lane == LPS - 1) h[QPL - 1] = s[mt_lag_base(k0 + CH)];
+#pragma unroll
+      for (int q = 0; q < QPL; q++) {      // X_624 is the new X_0
+        const int kr = k0 + 4 * LPS * q;
+        if (kr <= 620 && 620 < kr + 4 * LPS && 4 * lane + kr == 620) {
+          b[q] = s[0];
+          h[q] = s[mt_lag_base(624)];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < QPL; q++) {
+        const int k = k0 + 4 * LPS * q + 4 * lane;
+        if (k >= 624) continue;
+        const uint4 a = A[c][q], f = F[q];
+        uint4 v;
+        v.x = mt_mix(a.x, a.y, f.y);
+        v.y = mt_mix(a.y, a.z, f.z);
+        v.z = mt_mix(a.z, a.w, f.w);
+        v.w = mt_mix(a.w, b[q], h[q]);
+        *reinterpret_cast<uint4*>(s + k) = v;
+        A[c][q] = v;
+        if (ob != nullptr) mt_emit<OM, false>(v, k, ob, 624, vec, d, eb);
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -162,6 +283,20 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   bool vec = !store || ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   if (LPS < 32) vec = __all_sync(0xFFFFFFFFu, vec);
+  if constexpr (LPS == 16) {
+    // Leading blocks that are whole for both streams of the warp run with
+    // the lanes' quads in registers (mt_blocks_reg); the rest as below.
+    uint64_t nb = (n - j) / 624;
+    if (store) {
+      const uint64_t w = nv > j ? (nv - j) / 624 : 0;
+      if (w < nb) nb = w;
+    }
+    const uint32_t nb32 = __reduce_min_sync(0xFFFFFFFFu, nb > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)nb);
+    if (nb32 > 0) {
+      mt_blocks_reg<OM, LPS, QPL>(s, lane, store ? orow + j : nullptr, nb32, vec, &d, row * d.pitch + j);
+      j += (uint64_t)nb32 * 624;
+    }
+  }
   while (n - j >= 624) {
     bool whole = !store || j + 624 <= nv;
     if (LPS < 32) whole = __all_sync(0xFFFFFFFFu, whole);
