@@ -18,10 +18,15 @@
 
 namespace prng {
 
+// The tempering's left shifts, 7 and 15, as multiplies by 2^7 and 2^15 from
+// the constant bank: they then run on the FMA pipe rather than the integer
+// ALU, which the twist and the right shifts keep busy.
+__constant__ uint32_t c_mt_shl[2] = {1u << 7, 1u << 15};
+
 __device__ __forceinline__ uint32_t mt_temper(uint32_t t) {
   t ^= t >> 11;
-  t ^= (t << 7) & 0x9D2C5680u;
-  t ^= (t << 15) & 0xEFC60000u;
+  t ^= (t * c_mt_shl[0]) & 0x9D2C5680u;
+  t ^= (t * c_mt_shl[1]) & 0xEFC60000u;
   t ^= t >> 18;
   return t;
 }
@@ -36,9 +41,19 @@ __device__ __forceinline__ uint32_t mt_conv(uint32_t t) {
   else return t;
 }
 
+// The twist's matrix constant a = 0x9908B0DF (Section 3.7), read from the
+// constant bank so that its product with the low bit of y below stays a
+// multiply on the FMA pipe instead of becoming a select on the integer ALU,
+// which this kernel keeps busy.
+__constant__ uint32_t c_mt_a = 0x9908B0DFu;
+
+// X_k ^ upper, X_{k+1} ^ lower, shifted, times A (a when the low bit is set),
+// and the lag word: one new word of the twist.  The low bit of y is that of b.
 __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
   const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
-  return f ^ (y >> 1) ^ ((0u - (y & 1u)) & 0x9908B0DFu);
+  uint32_t mag;
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(mag) : "r"(b & 1u), "r"(c_mt_a));
+  return f ^ (y >> 1) ^ mag;
 }
 
 // Temper the new quad v = X_k .. X_{k+3} and hand it to the output: o[k]
@@ -167,11 +182,11 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
 // 4 LPS q + 4 u of every block, so after a twist its new quads are the old
 // ones of the next block).  The table in shared memory is kept as a mirror:
 // every new quad is stored there too, for the other lanes' lag reads, so
-// the only shared load of a quad is its aligned lag quad (mt_lag_base).  The
-// word after a quad and the word after its lag quad come from lane u+1 by a
-// shuffle; the group's last lane takes lane 0's next row (of the next chunk,
-// for the chunk's last row, whose lag word it loads), and the table's last
-// quad, whose next word is the new X_0, loads both.
+// the only shared loads of a quad are its aligned lag quad (mt_lag_base)
+// and, for the group's last lane only, the two words after the row (its
+// X_{k+4} and lag word); the other lanes get those from lane u+1 by a
+// shuffle.  The table's last quad, whose next word is the new X_0, loads
+// both too.
 template <int OM, int LPS, int QPL>
 __device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o, uint64_t nb,
                                               bool vec, const FillDesc* d, uint64_t e0) {
@@ -205,19 +220,14 @@ __device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o
       uint32_t b[QPL], h[QPL];
 #pragma unroll
       for (int q = 0; q < QPL; q++) {
-        uint32_t na = A[c][q].x, nf = F[q].x;
-        if (lane == 0) {
-          if (q + 1 < QPL) {
-            na = A[c][q + 1].x;
-            nf = F[q + 1].x;
-          } else if (c + 1 < NCH) {
-            na = A[c + 1][0].x;          // still the old word: chunk c+1 comes later
-          }
+        b[q] = __shfl_sync(0xFFFFFFFFu, A[c][q].x, (lane + 1) & (LPS - 1), LPS);
+        h[q] = __shfl_sync(0xFFFFFFFFu, F[q].x, (lane + 1) & (LPS - 1), LPS);
+        const int kn = k0 + 4 * LPS * (q + 1);   // the next row's first quad (old)
+        if (kn < 624 && lane == LPS - 1) {       // predicated loads, no selects
+          b[q] = s[kn];
+          h[q] = s[mt_lag_base(kn)];
         }
-        b[q] = __shfl_sync(0xFFFFFFFFu, na, (lane + 1) & (LPS - 1), LPS);
-        h[q] = __shfl_sync(0xFFFFFFFFu, nf, (lane + 1) & (LPS - 1), LPS);
       }
-      if (k0 + CH < 624 && lane == LPS - 1) h[QPL - 1] = s[mt_lag_base(k0 + CH)];
 #pragma unroll
       for (int q = 0; q < QPL; q++) {      // X_624 is the new X_0
         const int kr = k0 + 4 * LPS * q;

@@ -73,14 +73,16 @@ class Client:
 class Server:
     def __init__(self, client_specs, n_streams: int = 1024, mem_cap: float = 40e9,
                  max_inflight: int = 2, beta: float = ISING_BETA, keep_results: bool = False,
-                 max_active: int = 0, half_sweeps_per_tick: int = 1):
+                 max_active: int = 0, half_sweeps_per_tick: int = 1, scan_limit: int = 1024):
         """max_active > 0 caps the requests in progress (1 = a plain FIFO queue,
         one request at a time, the baseline continuous batching is measured
         against).  half_sweeps_per_tick: Ising half-sweeps a running request
         advances per tick.  More means fewer ticks per run, but longer ticks
         that later arrivals wait behind; with the GPU busy on half-sweeps
         (the benchmark's mix), 1 gives the lowest latency at the same
-        throughput."""
+        throughput.  scan_limit: pending requests examined for admission per
+        tick (in arrival order); the rest wait, so the host work of a tick
+        stays bounded when the queue is long."""
         import torch
         self.torch = torch
         self.clients = [Client(i, g, lux, seed, n_streams)
@@ -92,6 +94,7 @@ class Server:
         self.max_inflight = max_inflight
         self.max_active = max_active
         self.hpt = max(1, int(half_sweeps_per_tick))
+        self.scan_limit = max(1, int(scan_limit))
         self.keep = keep_results
         self.t4, self.t8 = prng_ising_thresholds(beta)
         self.stream = torch.cuda.Stream()
@@ -190,14 +193,15 @@ class Server:
             taken = set()                      # clients admitted this tick (one request each)
             keep = collections.deque()
             active = len(running) + sum(len(f) for _, f in inflight)
+            scanned = 0
             while pending:                      # admission in arrival order
+                if scanned == self.scan_limit or (self.max_active and active >= self.max_active):
+                    break                       # the rest keep their places in the queue
+                scanned += 1
                 i = pending.popleft()
                 r = reqs[i]
                 c = self.clients[r.client]
                 need = self.request_bytes(r)
-                if self.max_active and active >= self.max_active:
-                    keep.append(i)
-                    continue
                 active += 1
                 if r.client in taken or c.busy is not None or self.mem_used + need > self.mem_cap:
                     keep.append(i)
@@ -230,6 +234,7 @@ class Server:
                         r.numbers = r.sweeps * r.L * r.L
                         c.busy = r
                         new_ising.append(i)
+            keep.extend(pending)
             pending = keep
             if new_ising:
                 running = np.concatenate([running, np.asarray(new_ising, np.int64)])
