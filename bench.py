@@ -840,7 +840,8 @@ def measure_serving(args):
     from paper_1003_1898_gb300 import serve as S
     from paper_1003_1898_gb300 import workloads as W
     specs = W.serving_clients(W.SERVE_CLIENTS)
-    out = {"clients": W.SERVE_CLIENTS, "streams_per_client": W.SERVE_STREAMS,
+    streams = getattr(args, "serve_streams", None) or W.SERVE_STREAMS
+    out = {"clients": W.SERVE_CLIENTS, "streams_per_client": streams,
            "mem_cap_bytes": W.SERVE_MEM_CAP, "half_sweeps_per_tick": args.serve_hpt,
            "rates": []}
     arms = [a for a in ("continuous", "queue") if a in args.serve_arms]
@@ -848,7 +849,7 @@ def measure_serving(args):
         row = {"rate_per_s": rate, "requests": args.serve_requests}
         raw = W.serving_requests(args.serve_requests, rate)
         for mode in arms:
-            srv = S.Server(specs, n_streams=W.SERVE_STREAMS, mem_cap=W.SERVE_MEM_CAP,
+            srv = S.Server(specs, n_streams=streams, mem_cap=W.SERVE_MEM_CAP,
                            max_active=1 if mode == "queue" else 0,
                            half_sweeps_per_tick=args.serve_hpt)
             try:
@@ -864,7 +865,7 @@ def measure_serving(args):
 
 def serving_main(argv):
     """The serving sweep alone: bench.py serving [--rates R ...] [--requests N]
-    [--arms continuous queue] [--hpt H].  Prints one JSON line."""
+    [--arms continuous queue] [--hpt H] [--streams S].  Prints one JSON line."""
     import torch
     import paper_1003_1898_gb300 as P
     from paper_1003_1898_gb300 import build as B
@@ -875,6 +876,8 @@ def serving_main(argv):
     ap.add_argument("--requests", dest="serve_requests", type=int, default=10000)
     ap.add_argument("--arms", dest="serve_arms", nargs="+", default=["continuous", "queue"])
     ap.add_argument("--hpt", dest="serve_hpt", type=int, default=1)
+    ap.add_argument("--streams", dest="serve_streams", type=int, default=None,
+                    help="streams per client (default: the workload's)")
     a = ap.parse_args(argv)
     B.build()
     P.lib()

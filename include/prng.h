@@ -144,13 +144,16 @@ int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
  * halves of splitmix64(x0)), and chunk c starts from T^(c*L) of it over
  * GF(2) (Appendix A, "XORShift", matrix form).  The XOR128 form may cut the
  * sequence into more, shorter chunks than asked (at least 131072 when n
- * allows 64 draws each; the output is the same), and allocates a
+ * allows 64 draws each; the output is the same), and takes a
  * stream-ordered scratch array of 16 bytes per chunk (PRNG_EALLOC if that
  * fails).  MT19937: x0 < 2^32, the sequence of init_genrand(x0); chunk c
  * starts from its table moved c*L words on, built in log2(n_chunks)
  * doubling passes of the jump polynomial (about 6 million word XORs per
  * chunk, so a few thousand chunks is the useful range), with a scratch
- * array of 2.5 KB per chunk.  Other generators return PRNG_EUNSUPPORTED. */
+ * array of 2.5 KB per chunk.  The scratch arrays come from a stream-ordered
+ * memory pool that the library creates on first use on each device and
+ * that keeps its memory until the process exits, so repeated jump fills do
+ * not allocate afresh.  Other generators return PRNG_EUNSUPPORTED. */
 int prng_fill_jump_u32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,
                        uint32_t *d_out, void *stream);
 int prng_fill_jump_f32(prng_gen_t gen, uint64_t x0, uint64_t n, uint32_t n_chunks,

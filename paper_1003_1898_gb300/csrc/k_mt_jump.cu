@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "scratch.cuh"
 
 namespace prng {
 
@@ -215,7 +216,7 @@ cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_c
   HostMt mt;
   mt.init((uint32_t)x0);
   uint32_t* S = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S), C * 624 * sizeof(uint32_t), s);
+  cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&S), C * 624 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(S, mt.mt, sizeof(mt.mt), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && first > 0)   // the start table moved `first` words on, in place
@@ -236,7 +237,7 @@ cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_c
     d.mode = mode;
     e = launch_fill_mt(d, default_tile(MT19937, 0), s);
   }
-  const cudaError_t ef = cudaFreeAsync(S, s);
+  const cudaError_t ef = scratch_free(S, s);
   return e != cudaSuccess ? e : ef;
 }
 

@@ -10,7 +10,13 @@
 //   RANLUX   24 words from the MLCG 40014 mod 2147483563 started at
 //            s mod 2147483563 (19780503 when that is 0), carry = (x_{-1} == 0)
 //   MT19937  init_genrand(lo32(s))
+//
+// Also the host helpers the launchers share: the SM count, and the
+// retained stream-ordered scratch pool of the jump fills.
+#include <mutex>
+
 #include "batch.cuh"
+#include "scratch.cuh"
 
 namespace prng {
 
@@ -112,6 +118,42 @@ int sm_count() {
   }
   return n;
 }
+
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_lock;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+}  // namespace
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> guard(g_pool_lock);
+    if (g_pool[dev] == nullptr) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;   // never trim: freed blocks stay for the next call
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+      }
+      g_pool[dev] = pool;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t scratch_free(void* p, cudaStream_t s) { return cudaFreeAsync(p, s); }
 
 cudaError_t launch_batch_seed(const BatchQueue& q, cudaStream_t s) {
   if (q.n_items == 0) return cudaSuccess;

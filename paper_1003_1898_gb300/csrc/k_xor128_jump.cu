@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "scratch.cuh"
 
 namespace prng {
 
@@ -173,7 +174,7 @@ cudaError_t launch_jump_xor128(uint64_t x0, uint64_t first, uint64_t n, uint32_t
   if ((v0[0] | v0[1] | v0[2] | v0[3]) == 0) v0[3] = 1;
 
   uint32_t* S = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S), 4 * C * sizeof(uint32_t), s);
+  cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&S), 4 * C * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   k_xor128_set_row<<<1, 1, 0, s>>>(S, C, 0, v0[0], v0[1], v0[2], v0[3]);
   e = cudaGetLastError();
@@ -193,7 +194,7 @@ cudaError_t launch_jump_xor128(uint64_t x0, uint64_t first, uint64_t n, uint32_t
     d.mode = f32 ? OUT_F32 : OUT_U32;
     e = launch_fill_simple(XOR128, d, default_tile(XOR128, 0), s);
   }
-  const cudaError_t ef = cudaFreeAsync(S, s);
+  const cudaError_t ef = scratch_free(S, s);
   return e != cudaSuccess ? e : ef;
 }
 

@@ -65,7 +65,7 @@ def batched_requests(n_requests: int = 20000, seed: int = 0xB47C, min_len: int =
 
 
 SERVE_CLIENTS = 512
-SERVE_STREAMS = 1024          # divides L*L/2 for every Ising size below
+SERVE_STREAMS = 4096          # divides L*L/2 for every Ising size below
 SERVE_ISING_L = (256, 1024, 4096)
 SERVE_SWEEPS = 16
 SERVE_MEM_CAP = 40e9

@@ -7,7 +7,7 @@
   generator -- is compared with the oracle on its first, middle and last
   streams, including the element cut at n_valid.
 * Serving: checkerboard Ising runs at the serving sizes (L = 1024 for 16
-  sweeps, L = 4096 for 2 sweeps) on a client's 1,024 streams, with the draws
+  sweeps, L = 4096 for 2 sweeps) on a serving client's streams, with the draws
   stored (fill, then half-sweep) and consumed where they are made (fused),
   against the oracle's lattice, energy and magnetisation after every sweep.
 """
