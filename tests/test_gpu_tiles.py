@@ -88,3 +88,38 @@ def test_tile_parity_mt_jump(tile):
         assert np.all(got[n:] == np.uint32(2**32 - 7)), "write past the end"
     finally:
         P.prng_set_tile("mt19937", 0, *saved)
+
+
+@pytest.mark.parametrize("tile", tune.TILES["mt19937"])
+def test_tile_parity_mt_f64_and_fused(tile):
+    # The MT19937 tiles on the other output modes: doubles from pairs (whole
+    # 624-word blocks, so the register-resident block loop of the half-warp
+    # tiles runs) and the fused Ising half-sweep (whole and partial blocks).
+    saved = P.prng_get_tile("mt19937")
+    P.prng_set_tile("mt19937", 0, *tile)
+    try:
+        ns, nd = 37, 1300                          # 2600 draws: four whole blocks and a tail
+        h = P.prng_create("mt19937", 91, ns, 0)
+        try:
+            out = torch.empty(ns * nd, dtype=torch.float64, device="cuda")
+            P.prng_fill_f64(h, out, nd)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy().reshape(ns, nd),
+                                          oracle.fill_f64("mt19937", 91, ns, nd))
+        finally:
+            P.prng_destroy(h)
+        t4, t8 = P.prng_ising_thresholds(oracle.ISING_BETA)
+        L, ns = 256, 32                            # 1024 draws per stream per half-sweep
+        h = P.prng_create("mt19937", 92, ns, 0)
+        try:
+            spins = torch.ones((L, L), dtype=torch.int8, device="cuda")
+            for _ in range(3):
+                for colour in (0, 1):
+                    P.prng_ising_fused(h, spins, L, colour, t4, t8)
+            torch.cuda.synchronize()
+            want, _ = oracle.ising_run("mt19937", 92, ns, L, 3)
+            np.testing.assert_array_equal(spins.cpu().numpy(), want)
+        finally:
+            P.prng_destroy(h)
+    finally:
+        P.prng_set_tile("mt19937", 0, *saved)
