@@ -12,8 +12,8 @@
 // bytes of the stream's row, written without staging.  With half a warp per
 // stream, a lane keeps its own quads of the table in registers from one
 // 624-word block to the next (mt_blocks_reg), so the shared table serves
-// only the other lanes' lag reads; the kernel is bound by shared-memory
-// traffic and integer issue, not by the arithmetic alone.
+// only the other lanes' lag reads.  What bounds the kernel is then the
+// integer ALU: the twist's and the tempering's logic instructions.
 #include "batch.cuh"
 
 namespace prng {
@@ -47,8 +47,9 @@ __device__ __forceinline__ uint32_t mt_conv(uint32_t t) {
 // which this kernel keeps busy.
 __constant__ uint32_t c_mt_a = 0x9908B0DFu;
 
-// X_k ^ upper, X_{k+1} ^ lower, shifted, times A (a when the low bit is set),
-// and the lag word: one new word of the twist.  The low bit of y is that of b.
+// One new word of the twist: y = the upper bit of X_k (a) over the lower 31
+// bits of X_{k+1} (b), shifted right once, XOR a when y's low bit (b's) is
+// set, XOR the lag word f.
 __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
   const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
   uint32_t mag;
