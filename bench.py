@@ -97,13 +97,23 @@ KERNEL_SOURCES = {
 SHARED_SOURCES = ["common.cuh", "batch.cuh", "abi.cu"]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and with whitespace collapsed, so
+    that the hash below follows the code, not its comments."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_hash(gen):
-    """Hash of the sources a generator's fill kernels are built from."""
+    """Hash of the code (comments and layout ignored) of the sources a
+    generator's fill kernels are built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1003_1898_gb300", "csrc")
     for fn in SHARED_SOURCES + KERNEL_SOURCES[gen]:
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+            h.update(fn.encode() + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -49,3 +49,11 @@ def test_rank_partitions():
         assert bench.rank_seed_base(g, 0) == bench.SEED
         assert bench.rank_seed_base(g, 3) - bench.rank_seed_base(g, 2) == bench.shape(g)[0]
     assert bench.rank_jump_first(0) == 0 and bench.rank_jump_first(5) == 5 * bench.JUMP_N
+
+
+def test_source_hash_follows_code_not_comments():
+    a = "int f(int x) {  // add one\n  return x + 1; /* plain */\n}\n"
+    b = "int f(int x) {\n  /* a different\n     comment */ return x + 1;\n}  // end\n"
+    c = "int f(int x) { return x + 2; }\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
