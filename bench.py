@@ -869,6 +869,12 @@ def measure_serving(args):
             finally:
                 srv.close()
             row[mode] = S.latency_stats(done)
+            # where a tick's time goes: host work per tick, and the GPU time of
+            # its fills and half-sweeps, against the run's span
+            row[mode]["ticks"] = srv.stats["ticks"]
+            row[mode]["host_launch_s"] = srv.stats["launch_s"]
+            row[mode]["host_batcher_s"] = srv.stats["batcher_s"]
+            row[mode]["gpu_tick_s"] = srv.stats["gpu_s"]
         out["rates"].append(row)
     return out
 
@@ -885,7 +891,7 @@ def serving_main(argv):
                     default=[500.0, 1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 4000.0, 8000.0, 16000.0])
     ap.add_argument("--requests", dest="serve_requests", type=int, default=10000)
     ap.add_argument("--arms", dest="serve_arms", nargs="+", default=["continuous", "queue"])
-    ap.add_argument("--hpt", dest="serve_hpt", type=int, default=1)
+    ap.add_argument("--hpt", dest="serve_hpt", type=int, default=4)
     ap.add_argument("--streams", dest="serve_streams", type=int, default=None,
                     help="streams per client (default: the workload's)")
     a = ap.parse_args(argv)
@@ -1085,7 +1091,7 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 2000.0, 4000.0, 16000.0])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-arms", nargs="+", default=["continuous", "queue"])
-    ap.add_argument("--serve-hpt", type=int, default=1)
+    ap.add_argument("--serve-hpt", type=int, default=4)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

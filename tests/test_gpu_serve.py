@@ -38,7 +38,7 @@ def _results(reqs):
     return out
 
 
-@pytest.mark.parametrize("hpt", [1, 3])
+@pytest.mark.parametrize("hpt", [1, 3, 4])
 def test_mix_equals_oracle_and_clients_alone(hpt):
     # hpt: Ising half-sweeps per tick (3: one fill of three half-sweeps' draws,
     # read as column blocks of the stream rows, and three launches).
