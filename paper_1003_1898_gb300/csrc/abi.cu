@@ -132,7 +132,10 @@ int jump_impl(int gen, uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunk
 namespace {
 
 // Tiles compiled into the kernels, per generator family.
-bool tile_supported(int gen, Tile t) {
+bool tile_supported(int gen, Tile t, int p = 0) {
+  // RANLUX at p >= 97: also a 96-column staging tile (four delivered blocks
+  // per flush), compiled for those levels only.
+  if (gen == RANLUX && p >= 97 && t.threads == 64 && t.cols == 96 && t.stages == 1) return true;
   static const Tile simple[] = {{128, 32, 1}, {128, 32, 2}, {128, 64, 1}, {256, 32, 1}};
   static const Tile mlcg[] = {{128, 128, 1}, {256, 128, 1}};
   static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1}};
@@ -426,7 +429,7 @@ int prng_set_tile(prng_gen_t gen, uint32_t luxury, uint32_t threads, uint32_t co
     if (p < 0) return PRNG_ELUXURY;
   }
   const Tile t{(int)threads, (int)cols, (int)stages};
-  if (!tile_supported(g, t)) return PRNG_EUNSUPPORTED;
+  if (!tile_supported(g, t, p)) return PRNG_EUNSUPPORTED;
   g_tiles[tile_slot(g, p)] = t;
   return PRNG_OK;
 }

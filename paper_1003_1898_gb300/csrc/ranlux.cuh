@@ -193,7 +193,8 @@ __device__ __forceinline__ int swb_smem(uint32_t* ring, int ph, uint32_t& c, int
 // row-major tile of T rows x SPW words (KT staged columns each).
 template <int T, int KT, int P, int OM, bool LIMITED>
 __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, uint32_t* smem) {
-  static_assert(KT == 48, "the tile holds two blocks; its second half doubles as the scratch ring");
+  static_assert(KT % 24 == 0 && KT >= 48,
+                "the tile holds whole blocks; columns 24..47 double as the scratch ring");
   constexpr int SPW = KT + 4;
   const int tid = threadIdx.x;
   const uint64_t row = row0 + tid;
@@ -360,6 +361,9 @@ template <int P>
 cudaError_t ranlux_fill_p(const FillDesc& d, Tile t, cudaStream_t s) {
   return with_mode(d.mode, [&](auto m) {
     constexpr int OM = decltype(m)::value;
+    if constexpr (P >= 97) {   // fewer flushes where the chains, not the stores, set the pace
+      if (t.threads == 64 && t.cols == 96) return launch_l<64, 96, P, OM>(d, s);
+    }
     if (t.threads == 64) return launch_l<64, 48, P, OM>(d, s);
     if (t.threads == 256) return launch_l<256, 48, P, OM>(d, s);
     return launch_l<128, 48, P, OM>(d, s);

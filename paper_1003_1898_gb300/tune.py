@@ -26,17 +26,23 @@ TILES = {
     "ggl": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
     "ranecu": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
     "ranlux": [(64, 48, 1), (128, 48, 1), (256, 48, 1)],
+    "ranlux_high": [(64, 48, 1), (128, 48, 1), (256, 48, 1), (64, 96, 1)],   # p >= 97
     "ranmar": [(128, 128, 1), (256, 128, 1)],
     "mt19937": [(64, 624, 1), (128, 624, 1), (256, 624, 1), (32, 624, 2), (64, 624, 2),
                 (128, 624, 2), (256, 624, 2)],
 }
 
-# Workload shapes the tiles are tuned for (the roofline bulk fill).
+# Workload shapes the tiles are tuned for: the roofline bulk fill, and for
+# RANLUX at p >= 97 (not part of that fill) the luxury sweep.
 SHAPES = {"mt19937": (8192, 131072)}
 DEFAULT_SHAPE = (131072, 8192)
+LUXURY_SHAPE = (65536, 4096)
 
 
-def tiles_for(gen: str):
+def tiles_for(gen: str, luxury: int = 0):
+    """Tiles compiled for a generator (RANLUX at p >= 97 has one more)."""
+    if gen == "ranlux" and luxury >= 97:
+        return TILES["ranlux_high"]
     return TILES.get(gen, TILES["simple"])
 
 
@@ -83,10 +89,10 @@ def tune(gens=GEN_NAMES, luxuries=LUXURY_P + PLANAR_P[1:], reps: int = 5, verbos
         else:
             jobs.append((g, 0))
     for g, lux in jobs:
-        ns, nper = SHAPES.get(g, DEFAULT_SHAPE)
+        ns, nper = LUXURY_SHAPE if (g == "ranlux" and lux >= 97) else SHAPES.get(g, DEFAULT_SHAPE)
         before = prng_get_tile(g, lux)
         ms = {}
-        for t in tiles_for(g):   # a u32 fill plus an f32 fill, as the benchmark step does
+        for t in tiles_for(g, lux):   # a u32 fill plus an f32 fill, as the benchmark step does
             ms[",".join(map(str, t))] = (time_fill(g, t, ns, nper, lux, "u32", reps=reps) +
                                          time_fill(g, t, ns, nper, lux, "f32", reps=reps))
         best = min(ms, key=ms.get)

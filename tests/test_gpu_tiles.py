@@ -21,7 +21,7 @@ def _built():
     P.lib()
 
 
-CASES = [(g, t) for g in P.GEN_NAMES for t in tune.tiles_for(g)]
+CASES = [(g, t) for g in P.GEN_NAMES for t in tune.tiles_for(g, 223 if g == "ranlux" else 0)]
 
 
 @pytest.mark.parametrize("gen,tile", CASES, ids=[f"{g}-{'x'.join(map(str, t))}" for g, t in CASES])

@@ -78,7 +78,7 @@ def test_tile_table_accepts_compiled_tiles_only(lib):
         lux = 223 if gen == "ranlux" else 0
         saved = P.prng_get_tile(gen, lux)
         try:
-            for t in tune.tiles_for(gen):
+            for t in tune.tiles_for(gen, lux):
                 P.prng_set_tile(gen, lux, *t)
                 assert tuple(P.prng_get_tile(gen, lux)) == tuple(t)
             with pytest.raises(P.PrngError) as e:
@@ -86,6 +86,24 @@ def test_tile_table_accepts_compiled_tiles_only(lib):
             assert e.value.code == -7
         finally:
             P.prng_set_tile(gen, lux, *saved)
+
+
+def test_wide_ranlux_tile_only_at_high_luxury(lib):
+    # The 96-column RANLUX tile is compiled for p >= 97 only.
+    saved = P.prng_get_tile("ranlux", 24)
+    try:
+        with pytest.raises(P.PrngError) as e:
+            P.prng_set_tile("ranlux", 24, 64, 96, 1)
+        assert e.value.code == -7
+    finally:
+        P.prng_set_tile("ranlux", 24, *saved)
+    for p in (97, 223, 389, 120, 240, 408):
+        saved = P.prng_get_tile("ranlux", p)
+        try:
+            P.prng_set_tile("ranlux", p, 64, 96, 1)
+            assert tuple(P.prng_get_tile("ranlux", p)) == (64, 96, 1)
+        finally:
+            P.prng_set_tile("ranlux", p, *saved)
 
 
 def test_tuned_tiles_apply(lib):
