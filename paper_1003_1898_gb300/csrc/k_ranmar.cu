@@ -96,14 +96,35 @@ __device__ __forceinline__ void ranmar_warps(const FillDesc& d, uint64_t row0, i
         if (on && (!LIMITED || rbase + col < d.limit)) put1<OM>(d, orow + col, rbase + col, v);
       }
     };
+    // Doubles of a 64-draw pair of steps, one per lane: lane l takes draws
+    // 2l and 2l + 1 of the pair (of the first step for l < 16, of the second
+    // for l >= 16), so every lane assembles a double and the warp writes 256
+    // contiguous bytes.
+    auto emit_pairs = [&](uint64_t col0, uint32_t va, uint32_t vb) {
+      const int src = (2 * l) & 31;
+      const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, va, src);
+      const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, va, src + 1);
+      const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, vb, src);
+      const uint32_t b1 = __shfl_sync(0xFFFFFFFFu, vb, src + 1);
+      st_pair<24>(orow + col0 + 2 * l, l < 16 ? a0 : a1, l < 16 ? b0 : b1);
+    };
     uint64_t g = 0;
     for (; g + 128 <= n; g += 128) {
+      uint32_t v[4];
 #pragma unroll
       for (int s = 0; s < 4; s++) {
         const uint32_t y = rl[32 * s] - rl[32 * ((s + 2) & 3)];
         *wp[s] = y;
         __syncwarp();
-        if (store) emit(g + 32 * s, out_word(y, s), true);
+        v[s] = out_word(y, s);
+        if constexpr (OM != OUT_F64 || LIMITED)
+          if (store) emit(g + 32 * s, v[s], true);
+      }
+      if constexpr (OM == OUT_F64 && !LIMITED) {
+        if (store) {
+          emit_pairs(g, v[0], v[1]);
+          emit_pairs(g + 64, v[2], v[3]);
+        }
       }
       C = ranmar_advance_c(C, 128);
     }
