@@ -14,10 +14,10 @@
 //  * prng_skip on an XOR128 handle: T^k applied to every stream's state.
 //  * The single-sequence fill from x0: chunk c of L draws starts from
 //    T^(cL) s0 (chunks are cut finer than asked when there are too few to
-//    fill the GPU).  The chunk starts are built in log2(C) doubling passes
-//    (starts [2^i, 2^(i+1)) from starts [0, 2^i) by (T^L)^(2^i)) in a
-//    stream-ordered scratch array, then the ordinary XOR128 fill kernel runs
-//    with one chunk per row.
+//    fill the GPU).  The chunk starts are built in log8(C) passes of three
+//    doubling levels each (starts [H, 8H) from starts [0, H) by products of
+//    the powers T^(L H), T^(2 L H), T^(4 L H)) in a stream-ordered scratch
+//    array, then the ordinary XOR128 fill kernel runs with one chunk per row.
 #include <algorithm>
 #include <mutex>
 
@@ -110,6 +110,26 @@ Gf2x128 step_power(uint64_t k, int shift = 0) {
 
 }  // namespace
 
+// x = M x on the device, M passed in the launch parameters.  Fully unrolled
+// over the 128 bits of x, so that every column word is a constant-bank
+// operand of its XOR and the state stays in registers.
+__device__ __forceinline__ void gf2_apply_dev(const Gf2x128& M, uint32_t x[4]) {
+  uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    const uint32_t xw = x[w];
+#pragma unroll
+    for (int b = 0; b < 32; b++) {
+      const uint32_t m = 0u - ((xw >> b) & 1u);
+      o0 ^= M.col[32 * w + b][0] & m;
+      o1 ^= M.col[32 * w + b][1] & m;
+      o2 ^= M.col[32 * w + b][2] & m;
+      o3 ^= M.col[32 * w + b][3] & m;
+    }
+  }
+  x[0] = o0; x[1] = o1; x[2] = o2; x[3] = o3;
+}
+
 // Rows [r0, r1) of a struct-of-arrays XOR128 state (pitch rows per word)
 // become M times row (r - src_off).  With src_off = 0 the update is in place
 // (each thread reads its row before writing it).
@@ -119,22 +139,37 @@ __global__ void __launch_bounds__(256) k_xor128_apply(const __grid_constant__ Gf
   const uint64_t r = r0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= r1) return;
   const uint64_t src = r - src_off;
-  uint32_t v[4];
+  uint32_t x[4];
 #pragma unroll
-  for (int i = 0; i < 4; i++) v[i] = state[i * pitch + src];
-  uint32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;
-#pragma unroll 4
-  for (int j = 0; j < 128; j++) {
-    const uint32_t m = 0u - ((v[j >> 5] >> (j & 31)) & 1u);
-    o0 ^= M.col[j][0] & m;
-    o1 ^= M.col[j][1] & m;
-    o2 ^= M.col[j][2] & m;
-    o3 ^= M.col[j][3] & m;
-  }
-  state[r] = o0;
-  state[pitch + r] = o1;
-  state[2 * pitch + r] = o2;
-  state[3 * pitch + r] = o3;
+  for (int i = 0; i < 4; i++) x[i] = state[i * pitch + src];
+  gf2_apply_dev(M, x);
+#pragma unroll
+  for (int i = 0; i < 4; i++) state[i * pitch + r] = x[i];
+}
+
+struct Gf2x128x3 {
+  Gf2x128 m[3];   // T^E, T^(2E), T^(4E)
+};
+
+// Three doubling levels in one pass: with the chunk starts [0, H) known,
+// chunk r = j H + s (j = 1..7, s < H) starts at T^(j E) applied to start
+// s, E = L H the draws of H chunks.  One thread per r < C applies the
+// powers T^E, T^(2E), T^(4E) picked by the bits of j (at most three
+// products), so the host multiplies no matrices and a pass is one launch.
+__global__ void __launch_bounds__(256) k_xor128_apply3(const __grid_constant__ Gf2x128x3 P,
+                                                       uint32_t* state, uint64_t pitch,
+                                                       uint64_t H, uint64_t C) {
+  const uint64_t r = H + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= C || r >= 8 * H) return;
+  const uint64_t j = r / H, s = r - j * H;
+  uint32_t x[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) x[i] = state[i * pitch + s];
+  if (j & 4) gf2_apply_dev(P.m[2], x);
+  if (j & 2) gf2_apply_dev(P.m[1], x);
+  if (j & 1) gf2_apply_dev(P.m[0], x);
+#pragma unroll
+  for (int i = 0; i < 4; i++) state[i * pitch + r] = x[i];
 }
 
 __global__ void k_xor128_set_row(uint32_t* state, uint64_t pitch, uint64_t row, uint32_t x,
@@ -179,10 +214,22 @@ cudaError_t launch_jump_xor128(uint64_t x0, uint64_t first, uint64_t n, uint32_t
   k_xor128_set_row<<<1, 1, 0, s>>>(S, C, 0, v0[0], v0[1], v0[2], v0[3]);
   e = cudaGetLastError();
   if (e == cudaSuccess && first > 0) e = apply_rows(step_power(first), S, C, 0, 1, 0, s);  // to `first`
-  // Pass i: chunks [2^i, 2^(i+1)) from chunks [0, 2^i) by T^(L 2^i).
+  // Pass i: chunks [H, 8H) from chunks [0, H), H = 8^i, by T^(j L H).
   int i = 0;
-  for (uint64_t half = 1; e == cudaSuccess && half < C; half <<= 1, i++)
-    e = apply_rows(step_power(L, i), S, C, half, (2 * half < C ? 2 * half : C), half, s);
+  for (uint64_t H = 1; e == cudaSuccess && H < C; H <<= 3, i += 3) {
+    Gf2x128x3 P;
+    P.m[0] = step_power(L, i);
+    P.m[1] = step_power(L, i + 1);
+    P.m[2] = step_power(L, i + 2);
+    const uint64_t rows = std::min<uint64_t>(C, 8 * H) - H;
+    const uint64_t blocks = (rows + 255) / 256;
+    if (blocks > 0x7FFFFFFFull) {
+      e = cudaErrorInvalidValue;
+      break;
+    }
+    k_xor128_apply3<<<(unsigned)blocks, 256, 0, s>>>(P, S, C, H, C);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     FillDesc d{};
     d.state = S;
