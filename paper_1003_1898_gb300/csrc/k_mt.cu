@@ -188,9 +188,9 @@ __device__ __forceinline__ void mt_twist(uint32_t* s, int lane, uint32_t* o, int
 // X_{k+4} and lag word); the other lanes get those from lane u+1 by a
 // shuffle.  The table's last quad, whose next word is the new X_0, loads
 // both too.
-template <int OM, int LPS, int QPL>
+template <int OM, int LPS, int QPL, bool VEC>
 __device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o, uint64_t nb,
-                                              bool vec, const FillDesc* d, uint64_t e0) {
+                                              const FillDesc* d, uint64_t e0) {
   constexpr int CH = 4 * LPS * QPL, NCH = (624 + CH - 1) / CH;
   static_assert(CH <= 227, "a chunk may not reach its own lags");
   static_assert((LPS & (LPS - 1)) == 0, "lane u+1 is taken modulo a power of two");
@@ -249,7 +249,7 @@ __device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o
         v.w = mt_mix(a.w, b[q], h[q]);
         *reinterpret_cast<uint4*>(s + k) = v;
         A[c][q] = v;
-        if (ob != nullptr) mt_emit<OM, false>(v, k, ob, 624, vec, d, eb);
+        if (ob != nullptr) mt_emit<OM, false>(v, k, ob, 624, VEC, d, eb);
       }
       __syncwarp();
     }
@@ -305,8 +305,11 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
       if (w < nb) nb = w;
     }
     const uint32_t nb32 = __reduce_min_sync(0xFFFFFFFFu, nb > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)nb);
-    if (nb32 > 0) {
-      mt_blocks_reg<OM, LPS, QPL>(s, lane, store ? orow + j : nullptr, nb32, vec, &d, row * d.pitch + j);
+    if (nb32 > 0) {   // vec is the same for the whole warp
+      if (vec)
+        mt_blocks_reg<OM, LPS, QPL, true>(s, lane, store ? orow + j : nullptr, nb32, &d, row * d.pitch + j);
+      else
+        mt_blocks_reg<OM, LPS, QPL, false>(s, lane, store ? orow + j : nullptr, nb32, &d, row * d.pitch + j);
       j += (uint64_t)nb32 * 624;
     }
   }
