@@ -49,12 +49,22 @@ __constant__ uint32_t c_mt_a = 0x9908B0DFu;
 
 // One new word of the twist: y = the upper bit of X_k (a) over the lower 31
 // bits of X_{k+1} (b), shifted right once, XOR a when y's low bit (b's) is
-// set, XOR the lag word f.
+// set, XOR the lag word f.  Written out as four integer instructions (merge,
+// shift, low bit, three-way XOR) and the multiply: left to itself the
+// compiler spends one more integer instruction per word on it.
 __device__ __forceinline__ uint32_t mt_mix(uint32_t a, uint32_t b, uint32_t f) {
-  const uint32_t y = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
-  uint32_t mag;
-  asm("mul.lo.u32 %0, %1, %2;" : "=r"(mag) : "r"(b & 1u), "r"(c_mt_a));
-  return f ^ (y >> 1) ^ mag;
+  uint32_t r;
+  asm("{\n\t"
+      ".reg .b32 y, m, l;\n\t"
+      "lop3.b32 y, %1, %2, 0x7FFFFFFF, 0xD8;\n\t"   // (b & 0x7FFFFFFF) | (a & 0x80000000)
+      "shr.u32 y, y, 1;\n\t"
+      "and.b32 l, %2, 1;\n\t"
+      "mul.lo.u32 m, l, %4;\n\t"                    // a or 0
+      "lop3.b32 %0, %3, y, m, 0x96;\n\t"            // f ^ y ^ m
+      "}"
+      : "=r"(r)
+      : "r"(a), "r"(b), "r"(f), "r"(c_mt_a));
+  return r;
 }
 
 // Temper the new quad v = X_k .. X_{k+3} and hand it to the output: o[k]
