@@ -138,14 +138,15 @@ bool tile_supported(int gen, Tile t, int p = 0) {
   if (gen == RANLUX && p >= 97 && t.threads == 64 && t.cols == 96 && t.stages == 1) return true;
   static const Tile simple[] = {{128, 32, 1}, {128, 32, 2}, {128, 64, 1}, {256, 32, 1}};
   static const Tile mlcg[] = {{128, 128, 1}, {256, 128, 1}};
-  static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1}};
+  static const Tile lux[] = {{64, 48, 1}, {128, 48, 1}, {256, 48, 1},
+                             {64, 56, 1}, {128, 56, 1}, {256, 56, 1}};   // 56: the per-row ring
   static const Tile mar[] = {{128, 128, 1}, {256, 128, 1}};
   static const Tile mt[] = {{64, 624, 1}, {128, 624, 1}, {256, 624, 1},
                             {32, 624, 2}, {64, 624, 2}, {128, 624, 2}, {256, 624, 2}};
   const Tile* list = simple;
   int n = 4;
   if ((gen == GGL || gen == RANECU) && t.cols == 128) { list = mlcg; n = 2; }
-  else if (gen == RANLUX) { list = lux; n = 3; }
+  else if (gen == RANLUX) { list = lux; n = 6; }
   else if (gen == RANMAR) { list = mar; n = 2; }
   else if (gen == MT19937) { list = mt; n = 7; }
   for (int i = 0; i < n; i++)

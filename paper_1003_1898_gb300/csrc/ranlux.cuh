@@ -301,6 +301,145 @@ __device__ __forceinline__ void ranlux_rows(const FillDesc& d, uint64_t row0, ui
   }
 }
 
+// The same fill with a per-row ring instead of a flushed tile: each
+// thread's delivered blocks go to a ring of 56 words (14 16-byte chunks) in
+// its shared row, and its warp writes the warp's 32 rows out 32 words (one
+// aligned 128-byte line per row, when the row pitch is a multiple of 32
+// words) at a time, as soon as 32 are pending.  The ring never holds more
+// than 31 + 24 words, the warp's rows share one schedule (same length and
+// start position), so the copy-out is a warp-level step with no CTA
+// barrier.  Used for u32/f32 plain fills whose copies are 16-byte aligned:
+// pitch a multiple of 4 and a start that leaves a multiple of 4 draws in
+// the open block.
+template <int T, int P, int OM>
+__device__ __forceinline__ void ranlux_rows_ring(const FillDesc& d, uint64_t row0, uint32_t* smem) {
+  constexpr int RC = 14, SPW = 4 * RC + 4;    // ring chunks; row pitch 15 chunks (odd: no conflicts)
+  static_assert(T % 32 == 0, "whole warps");
+  const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5;
+  const uint64_t row = row0 + tid;
+  const uint64_t nr = d.n_rows;
+  const bool active = row < nr;
+  uint32_t* out = static_cast<uint32_t*>(d.out);
+  const bool store = out != nullptr;
+  uint32_t* my = smem + tid * SPW;
+  const uint32_t* wrows = smem + (wi * 32) * SPW;   // the warp's 32 ring rows
+  const uint64_t wrow0 = row0 + (uint64_t)wi * 32;
+  const int fq = lane & 7, fr = lane >> 3;         // copy-out role: chunk fq of rows fr + 4 i
+
+  const uint64_t n = d.n_per;
+  const int pos0 = (int)d.pos;
+  uint64_t j = 0, fpos = 0;   // draws made / written out in this call
+  int wc = 0, fc = 0;         // ring chunk of the next block / of the next copy-out
+  int pend = 0;               // words in the ring not yet written out
+  uint32_t R[24];
+  uint32_t c = 0;
+
+  // k chunks (4 k words, k <= 8) of every row of the warp from ring chunk fc
+  // to row column fpos.
+  auto copy_out = [&](int k) {
+    __syncwarp();
+    if (store && fq < k) {
+      int ch = fc + fq;
+      if (ch >= RC) ch -= RC;
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const uint64_t rr = wrow0 + fr + 4 * i;
+        if (rr < nr)
+          st_chunk<OM, 24>(out + rr * d.pitch + fpos + 4 * fq,
+                           *reinterpret_cast<const uint4*>(wrows + (fr + 4 * i) * SPW + 4 * ch));
+      }
+    }
+    __syncwarp();
+    fpos += 4 * k;
+    fc += k;
+    if (fc >= RC) fc -= RC;
+    pend -= 4 * k;
+  };
+
+  if (pos0 < 24) {
+    // Finish the open block on a shared copy of the ring (words 32..55 of
+    // the row), writing its h draws to ring words 0..h-1.
+    uint32_t* sring = my + 32;
+    const int h = (int)((uint64_t)(24 - pos0) < n ? (uint64_t)(24 - pos0) : n);
+    for (int jj = 0; jj < 24; jj++) sring[jj] = active ? d.state[jj * nr + row] : 0u;
+    c = active ? d.state[24 * nr + row] : 0u;
+    const int ph = swb_smem<OM>(sring, 0, c, h, my, true);
+    j = h;
+    if (j == n) {   // the fill ends inside the open block
+      if (active) {
+        for (int jj = 0; jj < 24; jj++) {
+          const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
+          d.state[(uint64_t)jj * nr + row] = sring[src];
+        }
+        d.state[24 * nr + row] = c;
+        if (store)
+          for (int k = 0; k < h; k++) st_out(out + row * d.pitch + k, my[k]);
+      }
+      return;
+    }
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) R[jj] = sring[(jj + h) % 24] << 8;
+    pend = h;          // a multiple of 4
+    wc = h / 4;
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) R[jj] = active ? d.state[jj * nr + row] << 8 : 0u;
+    c = active ? d.state[24 * nr + row] : 0u;
+  }
+
+  while (n - j >= 24) {
+    discard_cycle<P>(R, c);
+    swb24(R, c);
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      int ch = wc + q;
+      if (ch >= RC) ch -= RC;
+      *reinterpret_cast<uint4*>(my + 4 * ch) =
+          make_uint4(lux_out<OM>(R[4 * q]), lux_out<OM>(R[4 * q + 1]), lux_out<OM>(R[4 * q + 2]),
+                     lux_out<OM>(R[4 * q + 3]));
+    }
+    wc += 6;
+    if (wc >= RC) wc -= RC;
+    pend += 24;
+    j += 24;
+    if (pend >= 32) copy_out(8);
+  }
+  if (pend > 0) copy_out(pend / 4);
+
+  if (j < n) {
+    // Tail: the discard in registers, then m < 24 draws on a shared copy
+    // (row words 0..23; the draws at 24..), stored by each thread.
+    const int m = (int)(n - j);
+    discard_cycle<P>(R, c);
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) my[jj] = R[jj] >> 8;
+    const int ph = swb_smem<OM>(my, 0, c, m, my + 24, true);
+    if (active) {
+      if (store)
+        for (int k = 0; k < m; k++) st_out(out + row * d.pitch + fpos + k, my[24 + k]);
+      for (int jj = 0; jj < 24; jj++) {
+        const int src = jj + ph < 24 ? jj + ph : jj + ph - 24;
+        d.state[(uint64_t)jj * nr + row] = my[src];
+      }
+      d.state[24 * nr + row] = c;
+    }
+    return;
+  }
+
+  if (active) {
+#pragma unroll
+    for (int jj = 0; jj < 24; jj++) d.state[jj * nr + row] = R[jj] >> 8;
+    d.state[24 * nr + row] = c;
+  }
+}
+
+template <int T, int P, int OM>
+__global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux_ring(const FillDesc d) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  ranlux_rows_ring<T, P, OM>(d, (uint64_t)blockIdx.x * T, smem);
+}
+
 template <int T, int KT, int P, int OM>
 __global__ void __launch_bounds__(T, 896 / T) k_fill_ranlux(const FillDesc d) {
   extern __shared__ uint32_t smem[];
@@ -355,12 +494,46 @@ static cudaError_t launch_l(const FillDesc& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Whether a plain fill can take the ring form: u32 or f32, every 16-byte
+// copy aligned (output, pitch, and the draws left in the open block).
+inline bool ranlux_ring_ok(const FillDesc& d) {
+  if (d.mode != OUT_U32 && d.mode != OUT_F32) return false;
+  if (d.pos < 24 && (d.pos & 3) != 0) return false;
+  return d.out == nullptr || (((reinterpret_cast<uintptr_t>(d.out) & 15) == 0) && (d.pitch & 3) == 0);
+}
+
+template <int T, int P, int OM>
+static cudaError_t launch_ring(const FillDesc& d, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)T * 60 * sizeof(uint32_t);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_fill_ranlux_ring<T, P, OM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fill_ranlux_ring<T, P, OM>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const uint64_t grid = (d.n_rows + T - 1) / T;
+  k_fill_ranlux_ring<T, P, OM><<<(unsigned)grid, T, bytes, s>>>(d);
+  return cudaGetLastError();
+}
+
 // Launchers of one luxury P for every compiled tile (defined once per P, in
 // k_ranlux_p<P>.cu, so that the luxury levels compile in parallel).
 template <int P>
 cudaError_t ranlux_fill_p(const FillDesc& d, Tile t, cudaStream_t s) {
+  const bool ring = t.cols == 56 && ranlux_ring_ok(d);
   return with_mode(d.mode, [&](auto m) {
     constexpr int OM = decltype(m)::value;
+    if constexpr (OM == OUT_U32 || OM == OUT_F32) {
+      if (ring) {   // cols = 56: the per-row ring with warp-level 128-byte copy-outs
+        if (t.threads == 64) return launch_ring<64, P, OM>(d, s);
+        if (t.threads == 256) return launch_ring<256, P, OM>(d, s);
+        return launch_ring<128, P, OM>(d, s);
+      }
+    }
     if constexpr (P >= 97) {   // fewer flushes where the chains, not the stores, set the pace
       if (t.threads == 64 && t.cols == 96) return launch_l<64, 96, P, OM>(d, s);
     }

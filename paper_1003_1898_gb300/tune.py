@@ -25,8 +25,10 @@ TILES = {
     "simple": [(128, 32, 1), (128, 32, 2), (128, 64, 1), (256, 32, 1)],
     "ggl": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
     "ranecu": [(128, 128, 1), (256, 128, 1), (128, 32, 1), (128, 64, 1)],
-    "ranlux": [(64, 48, 1), (128, 48, 1), (256, 48, 1)],
-    "ranlux_high": [(64, 48, 1), (128, 48, 1), (256, 48, 1), (64, 96, 1)],   # p >= 97
+    # cols = 56: a per-row ring written out 32 words at a time by each warp
+    "ranlux": [(64, 48, 1), (128, 48, 1), (256, 48, 1), (64, 56, 1), (128, 56, 1), (256, 56, 1)],
+    "ranlux_high": [(64, 48, 1), (128, 48, 1), (256, 48, 1), (64, 96, 1),   # p >= 97
+                    (64, 56, 1), (128, 56, 1)],
     "ranmar": [(128, 128, 1), (256, 128, 1)],
     "mt19937": [(64, 624, 1), (128, 624, 1), (256, 624, 1), (32, 624, 2), (64, 624, 2),
                 (128, 624, 2), (256, 624, 2)],

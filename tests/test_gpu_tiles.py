@@ -21,12 +21,14 @@ def _built():
     P.lib()
 
 
-CASES = [(g, t) for g in P.GEN_NAMES for t in tune.tiles_for(g, 223 if g == "ranlux" else 0)]
+CASES = [(g, t, 223 if g == "ranlux" else 0) for g in P.GEN_NAMES
+         for t in tune.tiles_for(g, 223 if g == "ranlux" else 0)]
+CASES += [("ranlux", t, 24) for t in tune.tiles_for("ranlux", 24)]
 
 
-@pytest.mark.parametrize("gen,tile", CASES, ids=[f"{g}-{'x'.join(map(str, t))}" for g, t in CASES])
-def test_tile_parity(gen, tile):
-    lux = 223 if gen == "ranlux" else 0
+@pytest.mark.parametrize("gen,tile,lux", CASES,
+                         ids=[f"{g}-{'x'.join(map(str, t))}-p{p}" for g, t, p in CASES])
+def test_tile_parity(gen, tile, lux):
     saved = P.prng_get_tile(gen, lux)
     P.prng_set_tile(gen, lux, *tile)
     try:
@@ -52,6 +54,41 @@ def test_tile_parity(gen, tile):
             P.prng_destroy(h)
     finally:
         P.prng_set_tile(gen, lux, *saved)
+
+
+@pytest.mark.parametrize("lux,tile", [(24, (128, 56, 1)), (24, (64, 56, 1)), (24, (256, 56, 1)),
+                                      (48, (128, 56, 1)), (223, (128, 56, 1)), (223, (64, 56, 1))])
+def test_ranlux_ring_positions(lux, tile):
+    # Fills whose start positions and lengths reach every branch of the ring
+    # form: fills that end inside the open block (4 draws, and 2), heads of
+    # 4..20 draws, copy-outs from every ring offset, tails of 1..23 draws;
+    # interleaved with fills that the launcher hands to the tiled form (odd
+    # lengths: a row pitch, or a start position, that is not a multiple of 4).
+    pieces = [8, 4, 2, 10, 100, 4, 76, 1, 3, 48, 252, 24, 5, 96, 1000, 12, 7, 1024, 20, 32, 56, 60]
+    ns = 301
+    saved = P.prng_get_tile("ranlux", lux)
+    P.prng_set_tile("ranlux", lux, *tile)
+    try:
+        ref = oracle.fill("ranlux", 91, ns, sum(pieces), luxury=lux)
+        h = P.prng_create("ranlux", 91, ns, lux)
+        try:
+            col = 0
+            for i, k in enumerate(pieces):
+                f32 = i % 3 == 2
+                out = torch.full((ns * k + 4,), -7, dtype=torch.int32, device="cuda")
+                (P.prng_fill_f32 if f32 else P.prng_fill_u32)(h, out, k)
+                torch.cuda.synchronize()
+                got = out[:ns * k].cpu().numpy().reshape(ns, k).view(np.uint32)
+                want = ref[:, col:col + k]
+                if f32:
+                    want = oracle.to_f32("ranlux", want).view(np.uint32)
+                np.testing.assert_array_equal(got, want, err_msg=f"piece {i} ({k} draws)")
+                assert np.all(out[ns * k:].cpu().numpy() == -7), f"piece {i} wrote past its rows"
+                col += k
+        finally:
+            P.prng_destroy(h)
+    finally:
+        P.prng_set_tile("ranlux", lux, *saved)
 
 
 @pytest.mark.parametrize("gen", ["ggl", "ranecu"])
