@@ -87,14 +87,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# Sources that make up each generator's fill kernels (besides the shared
-# headers and the dispatch in abi.cu).
+# Device sources that make up each generator's fill kernels (besides the
+# shared headers).  Which of them a launch runs is set by the launch tile,
+# which the recorded traffic is keyed on as well.
 KERNEL_SOURCES = {
     "ggl": ["k_mlcg.cu", "k_simple.cu"], "ranecu": ["k_mlcg.cu", "k_simple.cu"],
     "xor128": ["k_simple.cu"], "ranmar": ["k_ranmar.cu"],
     "ranlux": ["ranlux.cuh", "k_ranlux.cu", f"k_ranlux_p{RANLUX_P}.cu"], "mt19937": ["k_mt.cu"],
 }
-SHARED_SOURCES = ["common.cuh", "batch.cuh", "abi.cu"]
+SHARED_SOURCES = ["common.cuh", "batch.cuh"]
 
 
 def _code_only(text: str) -> str:
@@ -117,15 +118,18 @@ def kernel_sources_hash(gen):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(label, gen):
+def recorded_traffic(label, gen, tile=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current sources of that generator's kernels; else None."""
+    on the current sources of that generator's kernels and (when given) with
+    the launch tile in effect now; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
         entry = t["per_launch"].get(label)
         if entry is None or entry.get("sources") != kernel_sources_hash(gen):
+            return None
+        if tile is not None and list(entry.get("tile", [])) != list(tile):
             return None
         return entry["bytes"]
     except Exception:
@@ -629,7 +633,8 @@ def run_ours(args, rank, world, local_rank):
     dom = max(items, key=lambda it: per[it[0]]["ms"])
     dl = dom[0]
     roof = {"kernel": dl, "bound": "hbm", "achieved": per[dl]["gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": per[dl]["frac_hbm"], "traffic": recorded_traffic(dl, dom[1]),
+            "unit": "GB/s", "frac": per[dl]["frac_hbm"],
+            "traffic": recorded_traffic(dl, dom[1], P.prng_get_tile(dom[1], RANLUX_P if dom[1] == "ranlux" else 0)),
             "peak_source": f"{peak_kind} hbm_gbs (copy, read+write)",
             "algorithmic_bytes_per_launch": algorithmic_bytes(*dom)}
 

@@ -3,6 +3,8 @@ matches the roofline bulk-fill configuration (2^30 u32 and 2^30 f32 per
 generator, 131,072 streams x 8192 and MT19937 8192 x 131,072, two jump
 fills of 2^30), and the algorithmic bytes per launch are 4 B per output
 plus one read and one write of the state, per generator."""
+import json
+
 import pytest
 
 import bench
@@ -38,10 +40,21 @@ def test_algorithmic_bytes_per_launch(gen, state_bytes_per_stream):
     assert bench.algorithmic_bytes(f"{gen}_jump", gen, "jump", GIB) == 4 * GIB
 
 
-def test_recorded_traffic_needs_matching_sources():
+def test_recorded_traffic_needs_matching_sources_and_tile(tmp_path, monkeypatch):
     assert bench.recorded_traffic("no_such_label", "ggl") is None
     h = bench.kernel_sources_hash("ggl")
     assert len(h) == 16 and h != bench.kernel_sources_hash("mt19937")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({"per_launch": {
+        "ggl_u32": {"bytes": 123, "sources": h, "tile": [128, 128, 1]},
+        "mt19937_u32": {"bytes": 456, "sources": "0" * 16, "tile": [32, 624, 2]}}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda g: h)
+    assert bench.recorded_traffic("ggl_u32", "ggl", [128, 128, 1]) == 123
+    assert bench.recorded_traffic("ggl_u32", "ggl", (128, 128, 1)) == 123
+    assert bench.recorded_traffic("ggl_u32", "ggl", [128, 32, 1]) is None     # other tile
+    assert bench.recorded_traffic("mt19937_u32", "mt19937", [32, 624, 2]) is None  # other sources
 
 
 def test_rank_partitions():
