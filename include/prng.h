@@ -305,7 +305,7 @@ int prng_float_shift(prng_gen_t gen, uint32_t *shift);
  *     streams / 4 for GGL and RANECU, / 2 for MT19937, / the tile width
  *     otherwise); larger batches return PRNG_ESCRATCH and launch nothing.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current.
  *   - Every call shares the array and the previous call's contents remain
  *     there (the work counters are cleared at the start of each call): two
  *     calls whose work overlaps on the GPU -- for example calls on two
