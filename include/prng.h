@@ -150,7 +150,9 @@ int prng_set_state(prng_state *st, const void *h_buf, size_t bytes);
  * starts from its table moved c*L words on, built in log2(n_chunks)
  * doubling passes of the jump polynomial (about 6 million word XORs per
  * chunk, so a few thousand chunks is the useful range), with a scratch
- * array of 2.5 KB per chunk.  The scratch arrays come from a stream-ordered
+ * array of 2.5 KB per chunk.  The MT19937 form merges the chunks into fewer,
+ * longer ones when more are asked than one wave of warps holds (27 per SM,
+ * a warp per chunk; the output is the same).  The scratch arrays come from a stream-ordered
  * memory pool that the library creates on first use on each device and
  * that keeps its memory until the process exits, so repeated jump fills do
  * not allocate afresh.  Other generators return PRNG_EUNSUPPORTED. */

@@ -304,9 +304,10 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   bool vec = !store || ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   if (LPS < 32) vec = __all_sync(0xFFFFFFFFu, vec);
-  if constexpr (LPS == 16 && OM != OUT_ISING) {
-    // Leading blocks that are whole for both streams of the warp run with
-    // the lanes' quads in registers (mt_blocks_reg); the rest as below.
+  if constexpr (OM != OUT_ISING) {
+    // Leading blocks that are whole for both streams of the warp (or the
+    // warp's one stream) run with the lanes' quads in registers
+    // (mt_blocks_reg); the rest as below.
     // (Not for the fused half-sweep: its site updates need the registers,
     // and at 96 per thread the 8,192-stream fill no longer fits one wave.)
     uint64_t nb = (n - j) / 624;

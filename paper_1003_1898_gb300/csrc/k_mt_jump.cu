@@ -27,7 +27,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "common.cuh"
+#include "batch.cuh"
 #include "scratch.cuh"
 
 namespace prng {
@@ -211,6 +211,17 @@ cudaError_t launch_skip_mt(uint32_t* state, uint64_t n, uint64_t k, cudaStream_t
 
 cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_chunks,
                            void* d_out, int mode, cudaStream_t s) {
+  // Every chunk costs one application of a jump polynomial, the bulk of the
+  // call.  A warp per chunk (the fill's full-warp tile) keeps the GPU as busy
+  // as two chunks per warp do, so more chunks than that many warps (27 per
+  // SM, one wave) are merged into longer ones: any contiguous cut of the one
+  // sequence gives the same output.
+  const uint32_t wave = 27u * (uint32_t)sm_count();
+  Tile tile = default_tile(MT19937, 0);
+  if (n_chunks > wave) {
+    n_chunks = wave;
+    tile = Tile{64, 624, 1};
+  }
   const uint64_t L = (n + n_chunks - 1) / n_chunks;   // draws per chunk
   const uint64_t C = (n + L - 1) / L;                 // chunks, none empty
   HostMt mt;
@@ -235,7 +246,7 @@ cudaError_t launch_jump_mt(uint64_t x0, uint64_t first, uint64_t n, uint32_t n_c
     d.limit = n;
     d.pos = 624;          // fresh tables: the next output twists
     d.mode = mode;
-    e = launch_fill_mt(d, default_tile(MT19937, 0), s);
+    e = launch_fill_mt(d, tile, s);
   }
   const cudaError_t ef = scratch_free(S, s);
   return e != cudaSuccess ? e : ef;
