@@ -88,6 +88,24 @@ def test_tile_table_accepts_compiled_tiles_only(lib):
             P.prng_set_tile(gen, lux, *saved)
 
 
+def test_ranlux_ring_tiles_at_every_level(lib):
+    # The per-row ring form (56 columns) is compiled for every luxury level,
+    # single-staged only.
+    for p in (24, 48, 97, 223, 389, 120, 240, 408):
+        saved = P.prng_get_tile("ranlux", p)
+        try:
+            for t in ((64, 56, 1), (128, 56, 1), (256, 56, 1)):
+                P.prng_set_tile("ranlux", p, *t)
+                assert tuple(P.prng_get_tile("ranlux", p)) == t
+            with pytest.raises(P.PrngError) as e:
+                P.prng_set_tile("ranlux", p, 128, 56, 2)
+            assert e.value.code == -7
+        finally:
+            P.prng_set_tile("ranlux", p, *saved)
+    for t in tune.tiles_for("ranlux", 24):
+        assert t[1] != 96, "the 96-column tile is for p >= 97 only"
+
+
 def test_wide_ranlux_tile_only_at_high_luxury(lib):
     # The 96-column RANLUX tile is compiled for p >= 97 only.
     saved = P.prng_get_tile("ranlux", 24)
