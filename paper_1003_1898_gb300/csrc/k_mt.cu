@@ -272,7 +272,7 @@ __device__ __forceinline__ void mt_blocks_reg(uint32_t* s, int lane, uint32_t* o
 // whole warp (a 624-word block is twisted as partial or unaligned if either
 // stream needs it), and a half whose row is past the end (inactive) runs
 // along without touching memory outside shared memory.
-template <int OM, int LPS = 32, int QPL = 1>
+template <int OM, int LPS = 32, int QPL = 1, bool REG = true>
 __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint32_t* s, int lane,
                                           bool active = true) {
   uint32_t* gs = d.state + row * 624;
@@ -304,10 +304,11 @@ __device__ __forceinline__ void mt_stream(const FillDesc& d, uint64_t row, uint3
   // 16-byte output stores need the row position j to sit on a 16-byte boundary.
   bool vec = !store || ((reinterpret_cast<uintptr_t>(orow + j) & 15) == 0);
   if (LPS < 32) vec = __all_sync(0xFFFFFFFFu, vec);
-  if constexpr (OM != OUT_ISING) {
+  if constexpr (REG && OM != OUT_ISING) {
     // Leading blocks that are whole for both streams of the warp (or the
     // warp's one stream) run with the lanes' quads in registers
-    // (mt_blocks_reg); the rest as below.
+    // (mt_blocks_reg); the rest as below.  (Not in the batched kernel,
+    // whose 256-thread blocks it would push into spills.)
     // (Not for the fused half-sweep: its site updates need the registers,
     // and at 96 per thread the 8,192-stream fill no longer fits one wave.)
     uint64_t nb = (n - j) / 624;
@@ -374,7 +375,8 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_mt(const BatchQueue q) {
     __syncwarp();
     load_desc(&d, q.reqs[I.req].d, lane, 32);
     __syncwarp();
-    for (uint32_t k = 0; k < I.rows; k++) mt_stream<F32 ? OUT_F32 : OUT_U32>(d, I.row0 + k, table[wi], lane);
+    for (uint32_t k = 0; k < I.rows; k++)
+      mt_stream<F32 ? OUT_F32 : OUT_U32, 32, 1, false>(d, I.row0 + k, table[wi], lane);
   }
 }
 
