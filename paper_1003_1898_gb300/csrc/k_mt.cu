@@ -9,11 +9,12 @@
 // a chunk needs only a __syncwarp between its reads and its writes.  Each
 // new word is tempered and stored by the lane that produced it: a lane's 4
 // words are 16 bytes of a run of 512 (a warp) or 256 (a half) consecutive
-// bytes of the stream's row, written without staging.  With half a warp per
-// stream, a lane keeps its own quads of the table in registers from one
-// 624-word block to the next (mt_blocks_reg), so the shared table serves
-// only the other lanes' lag reads.  What bounds the kernel is then the
-// integer ALU: the twist's and the tempering's logic instructions.
+// bytes of the stream's row, written without staging.  In the fill kernels
+// a lane keeps its own quads of the table in registers from one 624-word
+// block to the next (mt_blocks_reg), so the shared table serves only the
+// other lanes' lag reads (the batched kernel keeps the shared-table form).
+// What bounds the kernel is then the integer ALU: the twist's and the
+// tempering's logic instructions.
 #include "batch.cuh"
 
 namespace prng {
