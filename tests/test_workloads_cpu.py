@@ -73,9 +73,10 @@ def lib():
     return P.lib()
 
 
-def test_tile_table_accepts_compiled_tiles_only(lib):
+@pytest.mark.parametrize("ranlux_p", [24, 223])
+def test_tile_table_accepts_compiled_tiles_only(lib, ranlux_p):
     for gen in P.GEN_NAMES:
-        lux = 223 if gen == "ranlux" else 0
+        lux = ranlux_p if gen == "ranlux" else 0
         saved = P.prng_get_tile(gen, lux)
         try:
             for t in tune.tiles_for(gen, lux):
